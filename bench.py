@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 fast Hough transform hot path.
+
+One step = every row of the hot path on one resident 4096 x 4096 uint8 edge
+map (5% Bernoulli edge pixels + 4 rasterised lines, seed 4096 + rank):
+
+  1. fht_full_quadrants   four quadrants, int32, written into the
+                          16381 x 8192 full Hough image (Section 3.3)
+  2. fhtshift             standalone regrouping of that image (Section 5)
+  3. fht_forward_range    slopes of [-15, 15] degrees (Q0 t<=1097, Q1 1<=t<=1097)
+  4. fht_adjoint          FP32 back-projection of a resident 16381 x 8192 FP32
+                          gradient onto the image (the transform's transpose)
+
+value = input megapixels per second over the whole step (all ranks).
+Timing: CUDA events on the stream the kernels run on, L2 flushed (a 512 MiB
+write) before every timed step, W >= 3 warm-up steps. Per-row times, the
+plain single-quadrant forward (the headline FHT at 4096^2 int32) and the
+batched path are reported under "rows".
+
+Multi-GPU: replicas only (each rank transforms its own image, no collective
+on the data path); value sums all ranks, time is the max over ranks.
+
+--impl reference times the CPU oracle (the plain C butterfly + numpy assembly)
+on the host cores, each step the same rows on a power-of-two crop of the image
+sized so that the whole run takes about 90 s.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("FHT Mpix/s and HBM GB/s (% of 8 TB/s) at 4096² int32; "
+          "batched & adjoint vs plain")
+UNIT = "Mpix/s"
+SIDE = 4096
+RANGE_DEG = (-15.0, 15.0)
+FLUSH_BYTES = 512 << 20
+NOMINAL_HBM_GBS = 8000.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--side", type=int, default=SIDE,
+                    help="image side (default 4096; smaller only for profiling runs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-rows", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, fl in enumerate(flags)
+                          if fl.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- oracle step
+
+def oracle_step(img):
+    """The step's rows by the CPU oracle (test infrastructure, timed only as a
+    baseline)."""
+    import numpy as np
+    import oracle as O
+    h, w = img.shape
+    F = O.full(img)
+    O.fhtshift_full(F, h, w)
+    lo, hi = O.angle_to_slopes(*RANGE_DEG, h, w)
+    for q in range(4):
+        if lo[q] >= 0:
+            O.range_slice(img, q, lo[q], hi[q])
+    g = np.random.default_rng(0).standard_normal(F.shape).astype(np.float32)
+    O.adjoint_full(g, h, w, "f32")
+
+
+def cpu_baseline(side: int):
+    from workloads import edges_and_lines
+    crop = 2048 if side >= 2048 else side
+    img = edges_and_lines(crop, crop, p_edge=0.05, n_lines=4, seed=4096)
+    t0 = time.perf_counter()
+    oracle_step(img)
+    dt = time.perf_counter() - t0
+    return {"value": crop * crop / 1e6 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full step (all four rows) on a {crop}x{crop} crop of the "
+                      f"same edge-map recipe, single-threaded C butterfly + numpy; "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from workloads import edges_and_lines
+    # size the per-step crop so that warm-up + timed steps stay near 90 s
+    budget_s = 90.0
+    probe = edges_and_lines(256, 256, p_edge=0.05, n_lines=4, seed=4096)
+    t0 = time.perf_counter()
+    oracle_step(probe)
+    t256 = time.perf_counter() - t0
+    crop = 256
+    while crop < args.side and (args.steps + args.warmup) * t256 * (2 * crop / 256) ** 2 \
+            * math.log2(2 * crop) / 8 <= budget_s:
+        crop *= 2
+    img = edges_and_lines(crop, crop, p_edge=0.05, n_lines=4, seed=4096)
+    for _ in range(args.warmup):
+        oracle_step(img)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(img)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = crop * crop / 1e6 / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{args.side}x{args.side} u8 edge map (5% edges + 4 lines): "
+                               "full 4-quadrant image, fhtshift, [-15,15] deg range, "
+                               "FP32 full adjoint", "sample_crop": f"{crop}x{crop}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step = all rows on a {crop}x{crop} crop"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_1811_06378_gb300 as fht
+    from workloads import edges_and_lines
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    S = args.side
+
+    img_h = edges_and_lines(S, S, p_edge=0.05, n_lines=4, seed=4096 + rank)
+    img = torch.from_numpy(img_h).to(dev)
+    R, Wf = fht.full_shape(S, S)
+    lo, hi = fht.angle_to_slopes(*RANGE_DEG, S, S)
+    used = [q for q in range(4) if lo[q] >= 0]
+    F = torch.empty((R, Wf), dtype=torch.int32, device=dev)
+    Fs = torch.empty_like(F)
+    n0, W0 = fht.query_shape(S, S, 0)
+    rng_out = {q: torch.empty((hi[q] - lo[q] + 1, fht.query_shape(S, S, q)[1]),
+                              dtype=torch.int32, device=dev) for q in used}
+    gen = torch.Generator(device=dev).manual_seed(7 + rank)
+    grad = torch.randn((R, Wf), generator=gen, device=dev, dtype=torch.float32)
+    gimg = torch.empty((S, S), dtype=torch.float32, device=dev)
+    ws_bytes = max(fht.workspace_size(S, S, fht.LAYOUT_FULL, 0, torch.uint8, torch.int32),
+                   fht.workspace_size(S, S, fht.LAYOUT_FULL, 0, torch.float32, torch.float32),
+                   fht.workspace_size(S, S, fht.LAYOUT_QUADRANT, 0, torch.uint8, torch.int32),
+                   fht.workspace_size(S, S, fht.LAYOUT_QUADRANT, 1, torch.uint8, torch.int32))
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    H0 = torch.empty((n0, W0), dtype=torch.int32, device=dev)
+
+    def row_full():
+        fht.full_quadrants(img, out=F, workspace=ws)
+
+    def row_shift():
+        fht.fhtshift(F, S, S, fht.LAYOUT_FULL, out=Fs)
+
+    def row_range():
+        for q in used:
+            fht.forward_range(img, q, lo[q], hi[q], out=rng_out[q], workspace=ws)
+
+    def row_adjoint():
+        fht.adjoint(grad, S, S, fht.LAYOUT_FULL, out=gimg, workspace=ws)
+
+    def step():
+        row_full()
+        row_shift()
+        row_range()
+        row_adjoint()
+
+    def timed(fn, reps):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            starts[i].record(stream)
+            fn()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = fht.launch_count()
+    fht.profile_begin()
+    step_ms = timed(step, args.steps)
+    prof = fht.profile_end()
+    launches = fht.launch_count() - launches0
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * S * S / 1e6 / (ms_per_step / 1e3)
+
+    # ---- per-row measurements (same flush discipline)
+    peak, peak_kind = load_peaks()
+    reps = max(10, min(args.steps, 50))
+    rows = {}
+    if not args.no_rows:
+        def row_entry(fn, alg_bytes, pixels):
+            t = statistics.median(timed(fn, reps))
+            return {"ms": t, "mpix_s": pixels / 1e6 / (t / 1e3),
+                    "alg_gbs": alg_bytes / (t / 1e3) / 1e9,
+                    "frac_of_measured_hbm": alg_bytes / (t / 1e3) / 1e9 / peak,
+                    "frac_of_8tbs": alg_bytes / (t / 1e3) / 1e9 / NOMINAL_HBM_GBS}
+        rows["forward_q0_int32"] = row_entry(
+            lambda: fht.forward(img, 0, out=H0, workspace=ws), S * S + n0 * W0 * 4, S * S)
+        rows["full_quadrants_int32"] = row_entry(row_full, S * S + R * Wf * 4, S * S)
+        rows["fhtshift_full_int32"] = row_entry(row_shift, 2 * R * Wf * 4, S * S)
+        rows["range_pm15deg_int32"] = row_entry(
+            row_range, S * S + sum(t.numel() for t in rng_out.values()) * 4, S * S)
+        rows["adjoint_full_f32"] = row_entry(row_adjoint, R * Wf * 4 + S * S * 4, S * S)
+
+    # ---- roofline of the dominant kernel (largest share of the timed step)
+    dom_name, (dom_launches, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    # the dominant row is the full four-quadrant transform
+    full_alg = S * S + R * Wf * 4
+    full_ms = rows.get("full_quadrants_int32", {}).get("ms")
+    achieved = full_alg / (full_ms / 1e3) / 1e9 if full_ms else None
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak if achieved else None, "traffic": None,
+        "peak_kind": f"{peak_kind} copy bandwidth",
+        "kernel": "fht_full_quadrants (all passes of the four quadrants)",
+        "alg_bytes_per_call": full_alg,
+        "dominant_launch_in_step": {"name": dom_name, "launches": dom_launches,
+                                    "avg_ms": dom_ms / max(dom_launches, 1),
+                                    "share": dom_ms / total_ms if total_ms else None},
+    }
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{S}x{S} u8 edge map (5% edges + 4 lines): full "
+                               "4-quadrant image, fhtshift, [-15,15] deg range, FP32 "
+                               "full adjoint", "l2": "flushed before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "kernel_times": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
+        "rows": rows,
+        "clocks": clk,
+    }
+
+    # ---- end to end through the public API with host buffers
+    if not args.no_e2e:
+        img_pin = torch.from_numpy(img_h).pin_memory()
+        grad_pin = torch.empty((R, Wf), dtype=torch.float32).pin_memory()
+        grad_pin.copy_(grad.cpu())
+        outs = {"F": torch.empty((R, Wf), dtype=torch.int32).pin_memory(),
+                "Fs": torch.empty((R, Wf), dtype=torch.int32).pin_memory(),
+                "g": torch.empty((S, S), dtype=torch.float32).pin_memory()}
+        outs.update({f"r{q}": torch.empty(tuple(rng_out[q].shape), dtype=torch.int32)
+                     .pin_memory() for q in used})
+
+        def e2e_step():
+            img.copy_(img_pin, non_blocking=True)
+            grad.copy_(grad_pin, non_blocking=True)
+            step()
+            outs["F"].copy_(F, non_blocking=True)
+            outs["Fs"].copy_(Fs, non_blocking=True)
+            outs["g"].copy_(gimg, non_blocking=True)
+            for q in used:
+                outs[f"r{q}"].copy_(rng_out[q], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k = max(3, min(args.steps, 20))
+        e_ms = statistics.mean(timed(e2e_step, k))
+        h2d = img.numel() + grad.numel() * 4
+        d2h = sum(t.numel() * t.element_size() for t in outs.values())
+        line["e2e"] = {"value": world * S * S / 1e6 / (e_ms / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": e_ms}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(S)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * fht.h -- C ABI of the GB300 (sm_103a) library for the Brady dyadic fast Hough
+ * transform and the modifications of Aliev, Ershov and Nikolaev, "On the use
+ * of FHT, its modification for practical applications and the structure of
+ * Hough image" (arXiv:1811.06378).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Images are row-major, h rows by w columns, element (y, x) at
+ * base[y * pitch + x]; every pitch is counted in ELEMENTS of the buffer's own
+ * type and must be >= the row length. Every data pointer is a DEVICE pointer
+ * (CUDA global memory) unless a comment says "host". `stream` is a
+ * cudaStream_t passed as void* (NULL = the legacy default stream). All calls
+ * that take a stream are asynchronous on it; argument checks happen on the
+ * host before anything is enqueued, and a call that returns an error has
+ * enqueued nothing.
+ *
+ * Ownership: the caller allocates and frees every device buffer, including
+ * the workspace (scratch for intermediate butterfly levels) whose size the
+ * *_workspace_size queries return. The library allocates no device memory.
+ * A workspace may be reused by calls that are ordered on one stream; calls
+ * running concurrently need separate workspaces.
+ *
+ * Errors: status codes only; nothing is thrown across the ABI.
+ *   FHT_EINVAL        bad sizes, pitches, dtypes, slope ranges, null pointers,
+ *                     or a workspace smaller than required
+ *   FHT_ECUDA         a CUDA launch or copy failed (see fht_last_cuda_error)
+ *   FHT_EUNSUPPORTED  a valid request this build does not implement
+ *   FHT_ETIMEOUT      a device-side bounded wait gave up (batched kernel)
+ *
+ * Geometry (Section 3.1): for the mostly-vertical quadrants Q0/Q1 the image is
+ * zero-padded virtually to n = next_pow2(h) rows and W = w + n columns taken
+ * cyclically; the quadrant has n slope rows t = 0..n-1 (t = n-1 is 45 deg) and
+ * W columns. The mostly-horizontal quadrants Q2/Q3 are the same on the
+ * transposed image: n = next_pow2(w), W = h + n. Padding is never stored.
+ *
+ * The transform (Brady's recursion, cited by the paper in Section 2 and drawn
+ * in Section 4, Figure 6): H_sigma[t][x] = sum_{y<n} P[y][(x + sigma*off_n(t,y)) mod W],
+ * off_n(t,y) = sum_{j=1..K} bit_{K-j}(y) * ceil(floor(t/2^(j-1))/2), n = 2^K.
+ * Q0 = sigma +1 on the image, Q1 = sigma -1 on the image, Q2 = sigma -1 on the
+ * transposed image, Q3 = sigma +1 on the transposed image.
+ *
+ * Supported (input -> accumulator) types: u8->i32, i32->i32, u8->f32, f32->f32.
+ * Integer accumulation wraps modulo 2^32 (exact while the true sums fit);
+ * FP32 accumulation adds exactly the two operands the recursion names, in
+ * round-to-nearest, so results are reproducible bit for bit.
+ */
+#ifndef FHT_H
+#define FHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FHT_OK = 0,
+    FHT_EINVAL = 1,
+    FHT_ENOMEM = 2,
+    FHT_ECUDA = 3,
+    FHT_EUNSUPPORTED = 4,
+    FHT_ETIMEOUT = 5
+} fht_status;
+
+typedef enum { FHT_U8 = 0, FHT_I32 = 1, FHT_F32 = 2 } fht_dtype;
+
+/* Angle quadrants of Section 3.1: Q0 [-45,0] deg (mostly vertical, positive
+ * shift), Q1 [0,45], Q2 [45,90] (mostly horizontal), Q3 [90,135]. */
+typedef enum { FHT_Q0 = 0, FHT_Q1 = 1, FHT_Q2 = 2, FHT_Q3 = 3 } fht_quadrant;
+
+/* Layout of a Hough image: one quadrant (n x W), or the full image of
+ * Section 3.3 (all four quadrants on a power-of-two-padded image). */
+typedef enum { FHT_LAYOUT_QUADRANT = 0, FHT_LAYOUT_FULL = 1 } fht_layout;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *fht_status_string(fht_status s);
+
+/* The last CUDA error code seen by this library on the calling thread
+ * (cudaError_t as int; 0 if none). */
+int fht_last_cuda_error(void);
+
+/* ------------------------------------------------------------------ geometry
+ * Host-only, synchronous, no device access. */
+
+/* Shape of quadrant q of an h x w image (Section 3.1): *rows = n, *cols = W. */
+fht_status fht_query_shape(int h, int w, fht_quadrant q, int *rows, int *cols);
+
+/* Shape of the full Hough image (Section 3.3): the image is padded to
+ * h_p x w_p (next powers of two); *rows = 2*(h_p + w_p) - 3, *cols = h_p + w_p. */
+fht_status fht_full_shape(int h, int w, int *rows, int *cols);
+
+/* Which quadrant and slope a full-image row holds (Section 3.3, end): rows
+ * [0, h_p) are Q0 flipped (t = h_p-1-row), then Q1 t = 1..h_p-1, then Q2
+ * flipped t = w_p-2..0, then Q3 t = 1..w_p-1 (each seam's shared row kept once). */
+fht_status fht_full_row_to_quadrant(int h, int w, int row, int *q, int *t);
+
+/* Slope ranges for line angles in [phi_lo_deg, phi_hi_deg] (Section 4).
+ * Quadrant spans Q0 [-45,0], Q1 [0,45], Q2 [45,90], Q3 [90,135]; inside a
+ * quadrant with n slopes, slope t lies atan(t/(n-1)) away from the quadrant's
+ * t = 0 edge (0 deg for Q0/Q1, 90 deg for Q2/Q3) and is kept iff that angle is
+ * in the range. A seam row shared by two quadrants is kept in the first of
+ * Q0, Q1, Q2, Q3. t_lo[q] = t_hi[q] = -1 marks an unused quadrant.
+ * t_lo and t_hi are HOST arrays of 4 ints. */
+fht_status fht_angle_to_slopes(double phi_lo_deg, double phi_hi_deg, int h, int w,
+                               int *t_lo, int *t_hi);
+
+/* Bytes of device workspace needed by fht_forward, fht_forward_range,
+ * fht_full_quadrants and fht_adjoint on an h x w image with this layout,
+ * quadrant (ignored for FHT_LAYOUT_FULL) and type pair. May be 0. */
+fht_status fht_workspace_size(int h, int w, fht_layout layout, fht_quadrant q,
+                              fht_dtype in_t, fht_dtype acc_t, size_t *bytes);
+
+/* ------------------------------------------------------------------ forward */
+
+/* One quadrant of the Hough image (Sections 3.1-3.2).
+ * img  h x w image of type in_t, pitch in_pitch.
+ * out  n x W Hough image of type acc_t, pitch out_pitch >= W; row t = slope t,
+ *      column x = x0 of Section 3.1 (cyclic over the padded width). */
+fht_status fht_forward(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                       fht_quadrant q, void *out, fht_dtype acc_t, int64_t out_pitch,
+                       void *workspace, size_t workspace_bytes, void *stream);
+
+/* The angle-range variant (Section 4): only slopes t_lo..t_hi of quadrant q,
+ * computed by pruning the slope index space at every butterfly level (the
+ * levels compute only the slopes those outputs depend on). out has
+ * t_hi - t_lo + 1 rows of W columns; row k holds slope t_lo + k, bit-identical
+ * to row t_lo + k of fht_forward. 0 <= t_lo <= t_hi < n. */
+fht_status fht_forward_range(const void *img, fht_dtype in_t, int h, int w,
+                             int64_t in_pitch, fht_quadrant q, int t_lo, int t_hi,
+                             void *out, fht_dtype acc_t, int64_t out_pitch,
+                             void *workspace, size_t workspace_bytes, void *stream);
+
+/* The full Hough image (Section 3.3): the image is padded to h_p x w_p, the
+ * four quadrants are computed with width h_p + w_p, and their rows are written
+ * straight into the concatenated layout (Q0 flipped, Q1, Q2 flipped, Q3; one
+ * copy of each shared seam row). out is fht_full_shape rows x cols.
+ * apply_fhtshift != 0 additionally rotates every row as fhtshift does
+ * (Section 5), fused into the same stores. */
+fht_status fht_full_quadrants(const void *img, fht_dtype in_t, int h, int w,
+                              int64_t in_pitch, void *out, fht_dtype acc_t,
+                              int64_t out_pitch, int apply_fhtshift, void *workspace,
+                              size_t workspace_bytes, void *stream);
+
+/* fhtshift (Section 5): rotate every row of a Hough image so that its
+ * meaningful pixels form one run centred in the row, the black zone split to
+ * both edges. Row t of a quadrant with black-zone width b = W - w_in - t
+ * (w_in = w for Q0/Q1, h for Q2/Q3; w_p or h_p in the full layout) moves
+ * right by floor(b/2) + t for the positive-sign quadrants Q0/Q3 and by
+ * floor(b/2) for Q1/Q2; inverse != 0 undoes it. Out of place only
+ * (in and out must not overlap). h, w are the IMAGE's sizes; the Hough image's
+ * shape follows from them and the layout (q is ignored for the full layout).
+ * dtype FHT_I32 or FHT_F32. */
+fht_status fhtshift(const void *in, void *out, fht_dtype dtype, int h, int w,
+                    fht_layout layout, fht_quadrant q, int inverse, int64_t in_pitch,
+                    int64_t out_pitch, void *stream);
+
+/* ------------------------------------------------------------------ adjoint */
+
+/* Adjoint (transpose) of fht_forward (layout QUADRANT, quadrant q) or of
+ * fht_full_quadrants without fhtshift (layout FULL): back-projects a Hough
+ * image gradient onto the h x w image. Not in the paper: the transform is
+ * linear and this is its exact transpose, run as the butterfly levels in
+ * reverse (each merge becomes a split). grad_hough has the forward output's
+ * shape, type dtype (FHT_F32 or FHT_I32), pitch in_pitch; grad_img is h x w
+ * of the same type, pitch out_pitch, fully overwritten. For the full layout the
+ * four quadrant contributions are summed in the order Q0, Q1, Q2, Q3. */
+fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
+                       fht_layout layout, fht_quadrant q, int64_t in_pitch,
+                       void *grad_img, int64_t out_pitch, void *workspace,
+                       size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------------------ profiling
+ * Kernel-level timing for benchmarks; normal use never needs it. Not in the
+ * paper. While profiling is on, every kernel launch made by this library is
+ * bracketed by a pair of CUDA events recorded on the launch's own stream;
+ * fht_profile_end waits for those events and returns, per kernel name, the
+ * number of launches and their summed device time. */
+typedef struct {
+    char name[64];
+    int launches;
+    double total_ms;
+} fht_kernel_time;
+
+/* Start (or restart) recording; previous records are dropped. */
+fht_status fht_profile_begin(void);
+
+/* Stop recording, synchronize the recorded events and write up to `capacity`
+ * per-kernel totals (HOST array) to `out`; *count receives the number of
+ * distinct kernel names seen (may exceed capacity). */
+fht_status fht_profile_end(fht_kernel_time *out, int capacity, int *count);
+
+/* Number of kernel launches this library has issued since it was loaded. */
+long long fht_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FHT_H */

@@ -1,0 +1,303 @@
+"""GB300 (sm_103a) fast Hough transform: thin Python binding of libfht.so.
+
+Every function here marshals arguments to the C ABI declared in
+``include/fht.h`` and returns the output tensor; all arithmetic runs in the
+library's CUDA kernels. PyTorch supplies device memory and streams only. If the
+compiled library is missing, importing this package raises ImportError: there
+is no CPU fallback.
+
+The transform is Brady's dyadic fast Hough transform as used by Aliev,
+Ershov and Nikolaev (arXiv:1811.06378): quadrants of the Hough image
+(Section 3.1), the full four-quadrant image (Section 3.3), the angle-range
+variant (Section 4) and fhtshift (Section 5), plus the adjoint.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+__all__ = [
+    "Q0", "Q1", "Q2", "Q3", "LAYOUT_QUADRANT", "LAYOUT_FULL", "FHTError", "lib",
+    "query_shape", "full_shape", "full_row_to_quadrant", "angle_to_slopes",
+    "workspace_size", "forward", "forward_range", "full_quadrants", "fhtshift",
+    "adjoint", "FHTFunction", "profile_begin", "profile_end", "launch_count",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfht.so")
+
+Q0, Q1, Q2, Q3 = 0, 1, 2, 3
+LAYOUT_QUADRANT, LAYOUT_FULL = 0, 1
+_U8, _I32, _F32 = 0, 1, 2
+_DTYPE = {torch.uint8: _U8, torch.int32: _I32, torch.float32: _F32}
+
+
+class FHTError(RuntimeError):
+    """A libfht call returned a status other than FHT_OK."""
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; "
+            "g.build()'` (needs nvcc for sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    ip = ctypes.POINTER(ctypes.c_int)
+    sz = ctypes.c_size_t
+    sigs = {
+        "fht_status_string": (ctypes.c_char_p, [i]),
+        "fht_last_cuda_error": (i, []),
+        "fht_query_shape": (i, [i, i, i, ip, ip]),
+        "fht_full_shape": (i, [i, i, ip, ip]),
+        "fht_full_row_to_quadrant": (i, [i, i, i, ip, ip]),
+        "fht_angle_to_slopes": (i, [d, d, i, i, ip, ip]),
+        "fht_workspace_size": (i, [i, i, i, i, i, i, ctypes.POINTER(sz)]),
+        "fht_forward": (i, [vp, i, i, i, i64, i, vp, i, i64, vp, sz, vp]),
+        "fht_forward_range": (i, [vp, i, i, i, i64, i, i, i, vp, i, i64, vp, sz, vp]),
+        "fht_full_quadrants": (i, [vp, i, i, i, i64, vp, i, i64, i, vp, sz, vp]),
+        "fhtshift": (i, [vp, vp, i, i, i, i, i, i, i64, i64, vp]),
+        "fht_adjoint": (i, [vp, i, i, i, i, i, i64, vp, i64, vp, sz, vp]),
+        "fht_profile_begin": (i, []),
+        "fht_profile_end": (i, [vp, i, ip]),
+        "fht_launch_count": (ctypes.c_longlong, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _check(status: int, what: str) -> None:
+    if status != 0:
+        msg = lib.fht_status_string(status).decode()
+        cuda = lib.fht_last_cuda_error()
+        raise FHTError(f"{what}: {msg} (status {status}, last CUDA error {cuda})")
+
+
+def _ints(k: int):
+    return (ctypes.c_int * k)()
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev2d(t: torch.Tensor, name: str) -> tuple[int, int]:
+    """(dtype code, pitch) of a row-major 2-D CUDA tensor."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be 2-D with unit column stride")
+    if t.dtype not in _DTYPE:
+        raise ValueError(f"{name}: unsupported dtype {t.dtype}")
+    return _DTYPE[t.dtype], max(t.stride(0), t.shape[1])
+
+
+# ------------------------------------------------------------------ geometry
+
+def query_shape(h: int, w: int, q: int) -> tuple[int, int]:
+    r, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib.fht_query_shape(h, w, q, ctypes.byref(r), ctypes.byref(c)), "fht_query_shape")
+    return r.value, c.value
+
+
+def full_shape(h: int, w: int) -> tuple[int, int]:
+    r, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib.fht_full_shape(h, w, ctypes.byref(r), ctypes.byref(c)), "fht_full_shape")
+    return r.value, c.value
+
+
+def full_row_to_quadrant(h: int, w: int, row: int) -> tuple[int, int]:
+    q, t = ctypes.c_int(), ctypes.c_int()
+    _check(lib.fht_full_row_to_quadrant(h, w, row, ctypes.byref(q), ctypes.byref(t)),
+           "fht_full_row_to_quadrant")
+    return q.value, t.value
+
+
+def angle_to_slopes(phi_lo: float, phi_hi: float, h: int, w: int):
+    lo, hi = _ints(4), _ints(4)
+    _check(lib.fht_angle_to_slopes(phi_lo, phi_hi, h, w, lo, hi), "fht_angle_to_slopes")
+    return list(lo), list(hi)
+
+
+def workspace_size(h: int, w: int, layout: int, q: int, in_dtype: torch.dtype,
+                   acc_dtype: torch.dtype) -> int:
+    b = ctypes.c_size_t()
+    _check(lib.fht_workspace_size(h, w, layout, q, _DTYPE[in_dtype], _DTYPE[acc_dtype],
+                                  ctypes.byref(b)), "fht_workspace_size")
+    return b.value
+
+
+def _workspace(ws, nbytes: int, device) -> torch.Tensor | None:
+    if nbytes == 0:
+        return ws
+    if ws is None:
+        return torch.empty(nbytes, dtype=torch.uint8, device=device)
+    if ws.numel() * ws.element_size() < nbytes:
+        raise ValueError(f"workspace too small: need {nbytes} bytes")
+    return ws
+
+
+def _shape(t: torch.Tensor, shape, name: str) -> None:
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _nbytes(t) -> int:
+    return 0 if t is None else t.numel() * t.element_size()
+
+
+# ------------------------------------------------------------------ forward
+
+def forward(img: torch.Tensor, q: int = Q0, acc: torch.dtype = torch.int32,
+            out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    """Quadrant q of the Hough image of img: (n, W) tensor of dtype acc."""
+    it, ip = _dev2d(img, "img")
+    h, w = img.shape
+    n, W = query_shape(h, w, q)
+    if out is None:
+        out = torch.empty((n, W), dtype=acc, device=img.device)
+    _shape(out, (n, W), "out")
+    ot, op = _dev2d(out, "out")
+    ws = _workspace(workspace, workspace_size(h, w, LAYOUT_QUADRANT, q, img.dtype, acc),
+                    img.device)
+    _check(lib.fht_forward(_ptr(img), it, h, w, ip, q, _ptr(out), ot, op, _ptr(ws),
+                           _nbytes(ws), _stream(stream)), "fht_forward")
+    return out
+
+
+def forward_range(img: torch.Tensor, q: int, t_lo: int, t_hi: int,
+                  acc: torch.dtype = torch.int32, out: torch.Tensor | None = None,
+                  workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Slopes t_lo..t_hi of quadrant q: (t_hi - t_lo + 1, W) tensor."""
+    it, ip = _dev2d(img, "img")
+    h, w = img.shape
+    n, W = query_shape(h, w, q)
+    if out is None:
+        out = torch.empty((max(t_hi - t_lo + 1, 0), W), dtype=acc, device=img.device)
+    _shape(out, (t_hi - t_lo + 1, W), "out")
+    ot, op = _dev2d(out, "out")
+    ws = _workspace(workspace, workspace_size(h, w, LAYOUT_QUADRANT, q, img.dtype, acc),
+                    img.device)
+    _check(lib.fht_forward_range(_ptr(img), it, h, w, ip, q, t_lo, t_hi, _ptr(out), ot, op,
+                                 _ptr(ws), _nbytes(ws), _stream(stream)), "fht_forward_range")
+    return out
+
+
+def full_quadrants(img: torch.Tensor, acc: torch.dtype = torch.int32,
+                   apply_fhtshift: bool = False, out: torch.Tensor | None = None,
+                   workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Full four-quadrant Hough image of img (Section 3.3)."""
+    it, ip = _dev2d(img, "img")
+    h, w = img.shape
+    R, W = full_shape(h, w)
+    if out is None:
+        out = torch.empty((R, W), dtype=acc, device=img.device)
+    _shape(out, (R, W), "out")
+    ot, op = _dev2d(out, "out")
+    ws = _workspace(workspace, workspace_size(h, w, LAYOUT_FULL, 0, img.dtype, acc),
+                    img.device)
+    _check(lib.fht_full_quadrants(_ptr(img), it, h, w, ip, _ptr(out), ot, op,
+                                  int(bool(apply_fhtshift)), _ptr(ws), _nbytes(ws),
+                                  _stream(stream)), "fht_full_quadrants")
+    return out
+
+
+def fhtshift(hough: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: int = Q0,
+             inverse: bool = False, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+    """fhtshift (Section 5) of a quadrant or full Hough image of an h x w image."""
+    t, ip = _dev2d(hough, "hough")
+    expect = full_shape(h, w) if layout == LAYOUT_FULL else query_shape(h, w, q)
+    _shape(hough, expect, "hough")
+    if out is None:
+        out = torch.empty_like(hough)
+    _shape(out, expect, "out")
+    ot, op = _dev2d(out, "out")
+    if ot != t:
+        raise ValueError("out must have the dtype of hough")
+    _check(lib.fhtshift(_ptr(hough), _ptr(out), t, h, w, layout, q, int(bool(inverse)), ip,
+                        op, _stream(stream)), "fhtshift")
+    return out
+
+
+def adjoint(grad: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: int = Q0,
+            out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    """Adjoint of forward (layout QUADRANT) or full_quadrants (layout FULL)."""
+    t, ip = _dev2d(grad, "grad")
+    _shape(grad, full_shape(h, w) if layout == LAYOUT_FULL else query_shape(h, w, q), "grad")
+    if out is None:
+        out = torch.empty((h, w), dtype=grad.dtype, device=grad.device)
+    _shape(out, (h, w), "out")
+    ot, op = _dev2d(out, "out")
+    if ot != t:
+        raise ValueError("out must have the dtype of grad")
+    ws = _workspace(workspace, workspace_size(h, w, layout, q, grad.dtype, grad.dtype),
+                    grad.device)
+    _check(lib.fht_adjoint(_ptr(grad), t, h, w, layout, q, ip, _ptr(out), op, _ptr(ws),
+                           _nbytes(ws), _stream(stream)), "fht_adjoint")
+    return out
+
+
+# ------------------------------------------------------------------ profiling
+
+class _KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_int),
+                ("total_ms", ctypes.c_double)]
+
+
+def profile_begin() -> None:
+    """Bracket every following library launch with CUDA events on its stream."""
+    _check(lib.fht_profile_begin(), "fht_profile_begin")
+
+
+def profile_end() -> dict[str, tuple[int, float]]:
+    """Stop recording; {kernel name: (launches, summed device ms)}."""
+    cap = 64
+    arr = (_KernelTime * cap)()
+    cnt = ctypes.c_int()
+    _check(lib.fht_profile_end(ctypes.cast(arr, ctypes.c_void_p), cap, ctypes.byref(cnt)),
+           "fht_profile_end")
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms)
+            for i in range(min(cnt.value, cap))}
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library since it was loaded."""
+    return int(lib.fht_launch_count())
+
+
+class FHTFunction(torch.autograd.Function):
+    """Differentiable FP32 Hough transform: forward by the CUDA butterfly,
+    backward by the hand-written adjoint kernels (its exact transpose).
+
+    apply(x, layout=LAYOUT_FULL, q=Q0) for a 2-D float32 CUDA tensor x."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, layout: int = LAYOUT_FULL, q: int = Q0):
+        ctx.h, ctx.w = x.shape
+        ctx.layout, ctx.q = layout, q
+        x = x.contiguous()
+        if layout == LAYOUT_FULL:
+            return full_quadrants(x, acc=torch.float32)
+        return forward(x, q, acc=torch.float32)
+
+    @staticmethod
+    def backward(ctx, g: torch.Tensor):
+        gx = adjoint(g.contiguous(), ctx.h, ctx.w, ctx.layout, ctx.q)
+        return gx, None, None

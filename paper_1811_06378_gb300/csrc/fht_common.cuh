@@ -1,0 +1,75 @@
+// fht_common.cuh -- shared definitions of the GB300 fast Hough transform kernels.
+//
+// Terminology (Brady's dyadic recursion, cited by the paper in Section 2 and
+// drawn in Section 4, Figure 6):
+//   level k     the array after k butterfly levels: n/2^k strips of 2^k rows,
+//               row s*2^k + tau of the array = slope tau of strip s
+//   pass        m consecutive levels k0 -> k1 = k0 + m run by one launch.
+//
+// Pass identity used by every kernel: for a level-k1 strip S and a level-k0
+// slope a, the 2^m level-k1 slopes a*2^m + c (c < 2^m) are the m-level
+// transform of the 2^m level-k0 rows (S*2^m + s')*2^k0 + a, s' < 2^m, after
+// row s' is sheared by sigma*a*s' columns, because
+//   off_{2^k1}(a*2^m + c, s'*2^k0 + y) = a*s' + off_{2^m}(c, s') + off_{2^k0}(a, y)
+// for y < 2^k0 (expand the closed form: the top m bits of the row index meet
+// halvings of a*2^m + c that contribute a*2^(m-j) plus the c-terms). So each
+// pass is a set of independent "groups" (S, a), each a small FHT of 2^m
+// sheared rows over the full row width, tiled along the columns with a halo
+// of 2^m - 1 columns.
+//
+// Column coordinates. Level-k arrays are stored "compact": column X of the
+// cyclic width W is kept at p = (X + sigma_plus * 2^k) mod W, sigma_plus = 1 for
+// sigma = +1 and 0 for sigma = -1, and only p < w_c + 2^k is stored (w_c = the
+// image's content width): every other column of a level-k array is zero for
+// any image. In these coordinates a pass never reads across the cyclic wrap;
+// only the final level (2^K = n) maps back to X with one wrap.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fht {
+
+enum ElemType : int { kU8 = 0, kU16 = 1, kI32 = 2, kF32 = 3 };
+
+// One side of a pass: the level-k0 ("lo") or level-k1 ("hi") array.
+struct Side {
+    void *ptr;
+    int64_t pitch;   // elements
+    int type;        // ElemType
+    int rows;        // lo image: content rows h_c; otherwise n
+    int cols;        // lo image: content cols w_c; compact: w_c + 2^k; final: W
+};
+
+struct PassDesc {
+    Side lo, hi;
+    int lo_image;    // lo is the level-0 image (zero outside rows x cols)
+    int transpose;   // lo image is read transposed (quadrants Q2, Q3)
+    int hi_final;    // hi is the final level: user layout (rows mapped, X columns)
+    int accumulate;  // adjoint into the image: add to what is there
+    int n, W, K, k0, sigma;
+    int a_lo, a_count;   // level-k0 slopes of the groups (range pruning)
+    int s_count;         // strips at level k1
+    int tile_w;          // output columns per tile
+    int tiles;           // tiles per group
+    // final level only: slope t is row row_base + row_dir*t of the output,
+    // present for t in [t_first, t_last]
+    int t_first, t_last, row_base, row_dir;
+    // final level only: fhtshift rotation fused into the row mapping
+    int shift_on, shift_win, shift_inverse;
+};
+
+__host__ __device__ inline int64_t floor_mod(int64_t v, int64_t m) {
+    int64_t r = v % m;
+    return r < 0 ? r + m : r;
+}
+
+// fhtshift rotation of slope row t (Section 5): the w_in + t meaningful
+// columns start at floor(b/2), b = W - w_in - t; positive-sign quadrants carry
+// their meaningful run across the wrap, hence the extra t.
+__host__ __device__ inline int fhtshift_amount(int t, int W, int w_in, int sigma) {
+    int b = W - w_in - t;
+    return b / 2 + (sigma > 0 ? t : 0);
+}
+
+}  // namespace fht

@@ -1,0 +1,124 @@
+"""The C ABI without a GPU: the library loads, exports every declared symbol,
+its host-side geometry agrees with the oracle, and bad arguments are rejected
+before anything touches the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fht():
+    import __graft_entry__
+    __graft_entry__._builder().build()
+    import paper_1811_06378_gb300 as m
+    return m
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(fht\w*)\s*\(", text))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(fht):
+    syms = _declared_symbols()
+    assert "fht_forward" in syms and "fhtshift" in syms and len(syms) >= 12
+    for s in syms:
+        assert hasattr(fht.lib, s), s
+
+
+def test_shapes_match_oracle(fht):
+    for h, w in [(1, 1), (3, 7), (256, 256), (300, 129), (2048, 2048), (5, 1000)]:
+        for q in range(4):
+            assert fht.query_shape(h, w, q) == O.quadrant_geometry(h, w, q)
+        assert fht.full_shape(h, w) == O.full_geometry(h, w)
+
+
+def test_full_row_map_matches_oracle(fht):
+    for h, w in [(1, 1), (4, 4), (5, 12), (16, 3), (64, 32)]:
+        for r, (q, t) in enumerate(O.full_row_map(h, w)):
+            assert fht.full_row_to_quadrant(h, w, r) == (q, t)
+
+
+@pytest.mark.parametrize("rng_", [(-15, 15), (75, 105), (-45, 135), (-30, -10), (5, 44),
+                                  (50, 80), (100, 130), (0, 0), (45, 45), (90, 90),
+                                  (-45, -45), (135, 135), (10, 70)])
+@pytest.mark.parametrize("hw", [(2048, 2048), (256, 100), (1, 1), (7, 300)])
+def test_angle_to_slopes_matches_oracle(fht, rng_, hw):
+    assert fht.angle_to_slopes(float(rng_[0]), float(rng_[1]), *hw) == \
+        tuple(O.angle_to_slopes(float(rng_[0]), float(rng_[1]), *hw))
+
+
+def test_workspace_sizes(fht):
+    import torch
+    # a single pass needs no intermediate
+    assert fht.workspace_size(64, 64, fht.LAYOUT_QUADRANT, 0, torch.uint8, torch.int32) == 0
+    a = fht.workspace_size(4096, 4096, fht.LAYOUT_QUADRANT, 0, torch.uint8, torch.int32)
+    b = fht.workspace_size(4096, 4096, fht.LAYOUT_QUADRANT, 0, torch.int32, torch.int32)
+    # 2 passes: one level-6 intermediate, uint16 for uint8 images
+    assert 0 < a < b
+    assert a >= 4096 * (4096 + 64) * 2
+    full = fht.workspace_size(4096, 4096, fht.LAYOUT_FULL, 0, torch.float32, torch.float32)
+    assert full >= b
+
+
+EINVAL = 1
+
+
+def test_bad_arguments_rejected_on_host(fht):
+    L = fht.lib
+    fake = ctypes.c_void_p(0x10000)   # never dereferenced: checks fail first
+    null = ctypes.c_void_p(0)
+    st = ctypes.c_void_p(0)
+    U8, I32, F32 = 0, 1, 2
+    # null pointers
+    assert L.fht_forward(null, U8, 8, 8, 8, 0, fake, I32, 16, null, 0, st) == EINVAL
+    assert L.fht_forward(fake, U8, 8, 8, 8, 0, null, I32, 16, null, 0, st) == EINVAL
+    # sizes and quadrant
+    assert L.fht_forward(fake, U8, 0, 8, 8, 0, fake, I32, 16, null, 0, st) == EINVAL
+    assert L.fht_forward(fake, U8, 8, -1, 8, 0, fake, I32, 16, null, 0, st) == EINVAL
+    assert L.fht_forward(fake, U8, 8, 8, 8, 4, fake, I32, 16, null, 0, st) == EINVAL
+    assert L.fht_forward(fake, U8, 1 << 20, 8, 8, 0, fake, I32, 16, null, 0, st) == EINVAL
+    # pitches
+    assert L.fht_forward(fake, U8, 8, 8, 7, 0, fake, I32, 16, null, 0, st) == EINVAL
+    assert L.fht_forward(fake, U8, 8, 8, 8, 0, fake, I32, 15, null, 0, st) == EINVAL
+    # dtype pairs: float images cannot accumulate in int32
+    assert L.fht_forward(fake, F32, 8, 8, 8, 0, fake, I32, 16, null, 0, st) == EINVAL
+    assert L.fht_forward(fake, I32, 8, 8, 8, 0, fake, F32, 16, null, 0, st) == EINVAL
+    assert L.fht_forward(fake, 7, 8, 8, 8, 0, fake, I32, 16, null, 0, st) == EINVAL
+    # workspace required at 4096 x 4096 (two passes) but missing / too small
+    assert L.fht_forward(fake, U8, 4096, 4096, 4096, 0, fake, I32, 8192, null, 0, st) == EINVAL
+    assert L.fht_forward(fake, U8, 4096, 4096, 4096, 0, fake, I32, 8192, fake, 100, st) == EINVAL
+    # slope ranges
+    assert L.fht_forward_range(fake, U8, 8, 8, 8, 0, 3, 2, fake, I32, 16, null, 0, st) == EINVAL
+    assert L.fht_forward_range(fake, U8, 8, 8, 8, 0, -1, 2, fake, I32, 16, null, 0, st) == EINVAL
+    assert L.fht_forward_range(fake, U8, 8, 8, 8, 0, 0, 8, fake, I32, 16, null, 0, st) == EINVAL
+    # full image: output pitch below h_p + w_p
+    assert L.fht_full_quadrants(fake, U8, 5, 9, 9, fake, I32, 23, 0, null, 0, st) == EINVAL
+    # fhtshift: in place and bad dtype
+    assert L.fhtshift(fake, fake, I32, 8, 8, 1, 0, 0, 16, 16, st) == EINVAL
+    assert L.fhtshift(fake, ctypes.c_void_p(0x20000), U8, 8, 8, 1, 0, 0, 16, 16, st) == EINVAL
+    assert L.fhtshift(fake, ctypes.c_void_p(0x20000), I32, 8, 8, 2, 0, 0, 16, 16, st) == EINVAL
+    # adjoint: u8 gradients are not a thing; pitch too small
+    assert L.fht_adjoint(fake, U8, 8, 8, 0, 0, 16, fake, 8, null, 0, st) == EINVAL
+    assert L.fht_adjoint(fake, F32, 8, 8, 0, 0, 15, fake, 8, null, 0, st) == EINVAL
+    assert L.fht_adjoint(fake, F32, 8, 8, 0, 0, 16, fake, 7, null, 0, st) == EINVAL
+    # geometry queries
+    r = ctypes.c_int()
+    assert L.fht_query_shape(0, 4, 0, ctypes.byref(r), ctypes.byref(r)) == EINVAL
+    assert L.fht_full_row_to_quadrant(4, 4, 13, ctypes.byref(r), ctypes.byref(r)) == EINVAL
+    lo = (ctypes.c_int * 4)()
+    assert L.fht_angle_to_slopes(10.0, 5.0, 8, 8, lo, lo) == EINVAL
+    assert fht.lib.fht_status_string(EINVAL) == b"invalid argument"
