@@ -19,7 +19,9 @@ What is computed (Aliev, Ershov, Nikolaev, arXiv:1811.06378):
 * ``fhtshift``     per-row cyclic regrouping around the accumulator centre
                    (Section 5).
 * ``adjoint_*``    the transpose of each map (not in the paper; defined by the
-                   transform being linear).
+                   transform being linear), computed as the opposite-sign
+                   transform of the gradient because the dyadic offsets are
+                   symmetric in (t, y).
 
 The butterfly itself lives in ``fht_oracle.c`` (plain C, compiled on demand
 with gcc, no fast-math). Readings of points the paper leaves open:
@@ -331,8 +333,15 @@ def angle_to_slopes(phi_lo: float, phi_hi: float, h: int, w: int
 
 def adjoint_quadrant(G: np.ndarray, h: int, w: int, q: int,
                      kind: str = "f64") -> np.ndarray:
-    """Transpose of ``quadrant``: (n, W) gradient -> (h, w) image gradient."""
-    A = adjoint_butterfly(G, SIGMA[q], kind)
+    """Transpose of ``quadrant``: (n, W) gradient -> (h, w) image gradient.
+
+    The dyadic offsets are symmetric, off_n(t, y) = off_n(y, t) (pinned by the
+    tests), so the transpose sum_t G[t][(c - sigma*off(t, y)) mod W] is the
+    opposite-sign transform of G read as an n-row image:
+    sum_t G[t][(c + (-sigma)*off(y, t)) mod W]. Floating-point kinds add along
+    that recursion's tree; ``adjoint_butterfly`` (the transposed network) and
+    ``explicit_matrix`` are independent checks of the same map."""
+    A = butterfly(G, -SIGMA[q], kind)
     if TRANSPOSED[q]:
         return A[:w, :h].T.copy()
     return A[:h, :w].copy()
@@ -340,8 +349,8 @@ def adjoint_quadrant(G: np.ndarray, h: int, w: int, q: int,
 
 def adjoint_full(G: np.ndarray, h: int, w: int, kind: str = "f64") -> np.ndarray:
     """Transpose of ``full``: each full-image row's gradient goes back to the
-    quadrant row it came from; the quadrant adjoints are summed in the order
-    Q0, Q1, Q2, Q3."""
+    quadrant row it came from (rows dropped at the seams get zero); the
+    quadrant adjoints are summed in the order Q0, Q1, Q2, Q3."""
     hp, wp = next_pow2(h), next_pow2(w)
     W = hp + wp
     dt, _ = _CT[kind]
@@ -351,10 +360,20 @@ def adjoint_full(G: np.ndarray, h: int, w: int, kind: str = "f64") -> np.ndarray
         per_q[q][t] = G[r]
     acc = None
     for q in (Q0, Q1, Q2, Q3):
-        A = adjoint_butterfly(per_q[q], SIGMA[q], kind)
+        A = butterfly(per_q[q], -SIGMA[q], kind)
         part = A[:w, :h].T if TRANSPOSED[q] else A[:h, :w]
         acc = part.copy() if acc is None else (acc + part).astype(dt)
     return acc
+
+
+def adjoint_quadrant_transposed_network(G: np.ndarray, h: int, w: int, q: int,
+                                        kind: str = "f64") -> np.ndarray:
+    """The same transpose computed by the transposed butterfly network (levels
+    in reverse, each merge turned into a split): an independent check."""
+    A = adjoint_butterfly(G, SIGMA[q], kind)
+    if TRANSPOSED[q]:
+        return A[:w, :h].T.copy()
+    return A[:h, :w].copy()
 
 
 def explicit_matrix(h: int, w: int, q: int) -> np.ndarray:

@@ -31,6 +31,24 @@ def test_patterns_are_digital_segments(n):
         assert np.abs(T - ideal).max() <= K / 6 + 1e-12
 
 
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 64, 1024, 4096])
+def test_pattern_table_is_symmetric(n):
+    """off_n(t, y) = off_n(y, t): the slope-t pattern's offset at row y equals
+    the slope-y pattern's offset at row t. Checked on the oracle's table for
+    small n and on an independent vectorised evaluation of the closed form
+    (the sum of bit_{K-j}(y) * ceil(floor(t/2^(j-1))/2)) up to n = 4096. The
+    adjoint relies on it."""
+    K = n.bit_length() - 1
+    t = np.arange(n)[:, None]
+    y = np.arange(n)[None, :]
+    T = np.zeros((n, n), np.int64)
+    for j in range(1, K + 1):
+        T += ((y >> (K - j)) & 1) * (((t >> (j - 1)) + 1) // 2)
+    assert (T == T.T).all()
+    if n <= 64:
+        assert (O.pattern_table(n) == T).all()
+
+
 @pytest.mark.parametrize("n", [2, 4, 8])
 def test_small_patterns_equal_rounded_lines(n):
     """For n <= 8 every pattern is exactly the nearest-pixel digitisation of the
@@ -320,6 +338,24 @@ def test_adjoint_is_matrix_transpose(h, w):
         assert (O.quadrant(x, q).ravel() == M @ x.ravel()).all()
         sig = O.SIGMA[q]
         assert (O.adjoint_butterfly(G, sig, "i64") == O.brute_adjoint(G, sig, "i64")).all()
+        assert (O.adjoint_quadrant_transposed_network(G, h, w, q, "i64") == got).all()
+
+
+@pytest.mark.parametrize("h,w", [(64, 64), (100, 37), (33, 130)])
+def test_adjoint_float_agrees_with_transposed_network(h, w):
+    """The FP32 adjoint (opposite-sign recursion) and the FP32 transposed
+    network round differently but both stay within the FP32 bound of FP64."""
+    rng = np.random.default_rng(h)
+    for q in range(4):
+        n, W = O.quadrant_geometry(h, w, q)
+        G = rng.standard_normal((n, W)).astype(np.float32)
+        mass = float(np.abs(G.astype(np.float64)).sum())
+        ref = O.adjoint_quadrant(G.astype(np.float64), h, w, q, "f64")
+        for got in (O.adjoint_quadrant(G, h, w, q, "f32"),
+                    O.adjoint_quadrant_transposed_network(G, h, w, q, "f32")):
+            assert np.abs(got - ref).max() <= 1e-5 * mass
+        assert np.abs(ref - O.adjoint_quadrant_transposed_network(
+            G.astype(np.float64), h, w, q, "f64")).max() <= 1e-9 * mass
 
 
 @pytest.mark.parametrize("h,w", [(32, 32), (20, 13)])
