@@ -1,18 +1,23 @@
-"""Compile the CUDA library libfht.so in-tree for sm_103a (nvcc, no cmake)."""
+"""Compile the CUDA library libfht.so in-tree for sm_103a (nvcc, no cmake).
+
+Every csrc/*.cu is one translation unit; they compile in parallel and link
+into paper_1811_06378_gb300/_build/libfht.so (CUDA runtime linked statically).
+"""
 
 from __future__ import annotations
 
+import concurrent.futures as cf
+import glob
 import os
 import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
+OBJ = os.path.join(BUILD, "obj")
 LIB = os.path.join(BUILD, "libfht.so")
-SOURCES = [os.path.join(HERE, "csrc", "fht_api.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in os.listdir(os.path.join(HERE, "csrc"))
-                  if f.endswith((".cuh", ".h"))] + [os.path.join(ROOT, "include", "fht.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -21,18 +26,40 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
-        if all(os.path.getmtime(d) <= t for d in DEPS):
-            return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-shared",
-           "-Xcompiler", "-fPIC", "-Xptxas", "-v" if verbose else "-O3",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
+def _headers() -> list[str]:
+    return (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+            + [os.path.join(ROOT, "include", "fht.h")])
+
+
+def _compile(src: str, verbose: bool) -> str:
+    obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+    cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+           "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj + ".tmp"]
+    if verbose:
+        cmd += ["-Xptxas", "-v"]
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    os.replace(obj + ".tmp", obj)
+    return obj
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    os.makedirs(OBJ, exist_ok=True)
+    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    newest_header = max(os.path.getmtime(h) for h in _headers())
+    todo = []
+    for src in sources:
+        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(
+                os.path.getmtime(src), newest_header):
+            todo.append(src)
+    if todo:
+        with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
+            list(ex.map(lambda s: _compile(s, verbose), todo))
+    objs = [os.path.join(OBJ, os.path.basename(s)[:-3] + ".o") for s in sources]
+    if todo or not os.path.exists(LIB):
+        tmp = LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+        os.replace(tmp, LIB)
     return LIB
 
 

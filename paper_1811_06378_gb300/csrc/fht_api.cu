@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -11,6 +12,7 @@
 #include <vector>
 
 #include "../../include/fht.h"
+#include "fht_host.h"
 #include "fht_kernels.cuh"
 
 using namespace fht;
@@ -41,40 +43,35 @@ cudaEvent_t take_event() {
     return e;
 }
 
-// Counts a launch and, while profiling is on, brackets it with events on its
-// stream: construct right before the launch, call done() right after.
-class LaunchScope {
-  public:
-    LaunchScope(const char *name, cudaStream_t st) : st_(st) {
-        g_launches.fetch_add(1, std::memory_order_relaxed);
-        std::lock_guard<std::mutex> lk(g_prof_mu);
-        on_ = g_prof_on;
-        if (on_) {
-            rec_.name = name;
-            rec_.a = take_event();
-            rec_.b = take_event();
-            cudaEventRecord(rec_.a, st_);
-        }
+}  // namespace
+
+namespace fht {
+
+LaunchScope::LaunchScope(const char *name, cudaStream_t st) : st_(st) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    on_ = g_prof_on;
+    if (on_) {
+        name_ = name;
+        a_ = take_event();
+        b_ = take_event();
+        cudaEventRecord(a_, st_);
     }
-    void done() {
-        if (!on_) return;
-        cudaEventRecord(rec_.b, st_);
-        std::lock_guard<std::mutex> lk(g_prof_mu);
-        g_prof.push_back(rec_);
-        on_ = false;
-    }
+}
 
-  private:
-    cudaStream_t st_;
-    bool on_ = false;
-    ProfRec rec_;
-};
+void LaunchScope::done() {
+    if (!on_) return;
+    cudaEventRecord(b_, st_);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back(ProfRec{name_, a_, b_});
+    on_ = false;
+}
 
-template <typename T> const char *acc_name();
-template <> const char *acc_name<float>() { return "f32"; }
-template <> const char *acc_name<int32_t>() { return "i32"; }
+}  // namespace fht
 
-constexpr int kBlock = 256;
+namespace {
+
+constexpr int kBlock = 256;   // fhtshift kernel
 constexpr int kMaxLevelsPerPass = 6;
 constexpr int kMaxK = 15;            // n <= 32768
 constexpr int kMaxSide = 32768;
@@ -112,6 +109,8 @@ int split_levels(int K, int *m) {
 // Geometry and pass plan of one quadrant transform.
 struct QuadPlan {
     int q, sigma, transpose;
+    bool adjoint;
+    int in_elem, acc_elem;
     int h_c, w_c;       // content size of the (transposed) image
     int n, K, W;
     int w_in;           // meaningful width used by fhtshift
@@ -123,11 +122,19 @@ struct QuadPlan {
     size_t buf_bytes[2];
 };
 
-QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem) {
+// Plan of quadrant q. With `adjoint`, the plan is the transform's transpose:
+// the opposite-sign transform of the gradient (the dyadic offsets are
+// symmetric in slope and row), every level all W columns wide and cyclic.
+QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
+                   bool adjoint = false) {
     QuadPlan P{};
     P.q = q;
+    P.adjoint = adjoint;
+    P.in_elem = in_elem;
+    P.acc_elem = acc_elem;
     P.transpose = q >= 2;
     P.sigma = (q == 0 || q == 3) ? 1 : -1;
+    if (adjoint) P.sigma = -P.sigma;
     P.h_c = P.transpose ? w : h;
     P.w_c = P.transpose ? h : w;
     P.n = next_pow2(P.h_c);
@@ -147,9 +154,9 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem) {
         int k = P.k[p];
         int type = acc_elem;
         // u8 images summed over 2^k rows stay below 2^16 while k <= 8
-        if (acc_elem == kI32 && in_elem == kU8 && k <= 8) type = kU16;
+        if (acc_elem == kI32 && in_elem == kU8 && k <= 8 && !adjoint) type = kU16;
         P.lvl_type[p] = type;
-        P.lvl_cols[p] = std::min(P.W, P.w_c + (1 << k));
+        P.lvl_cols[p] = adjoint ? P.W : std::min(P.W, P.w_c + (1 << k));
         P.lvl_pitch[p] = (int64_t)align_up(P.lvl_cols[p], 64);
         size_t bytes = align_up((size_t)P.n * P.lvl_pitch[p] * elem_bytes(type), 256);
         size_t &slot = P.buf_bytes[(p - 1) % 2];
@@ -185,52 +192,44 @@ FinalMap full_map(int q, int hp, int wp) {
     }
 }
 
-int tile_width(int M) { return M >= 4 ? 128 : 256; }
-
-template <int M, typename AccT>
-__global__ void __launch_bounds__(kBlock) forward_pass_kernel(PassDesc d) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    forward_item<M, AccT>(d, blockIdx.y, blockIdx.x, reinterpret_cast<AccT *>(smem_raw));
-}
-
-template <int M, typename AccT>
-__global__ void __launch_bounds__(kBlock) adjoint_pass_kernel(PassDesc d) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    adjoint_item<M, AccT>(d, blockIdx.y, blockIdx.x, reinterpret_cast<AccT *>(smem_raw));
-}
-
-template <int M, typename AccT>
-cudaError_t launch_pass_t(const PassDesc &d, bool adjoint, cudaStream_t st) {
-    size_t smem = (size_t)item_smem_elems(M, d.tile_w) * sizeof(AccT);
-    dim3 grid(d.tiles, d.s_count * d.a_count);
-    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    char name[64];
-    snprintf(name, sizeof name, "%s_pass_m%d_%s%s", adjoint ? "adjoint" : "forward", M,
-             acc_name<AccT>(),
-             adjoint ? (d.lo_image ? "_to_image" : "") : (d.hi_final ? "_final" : ""));
-    auto k = adjoint ? adjoint_pass_kernel<M, AccT> : forward_pass_kernel<M, AccT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    LaunchScope scope(name, st);
-    k<<<grid, kBlock, smem, st>>>(d);
-    scope.done();
-    return cudaGetLastError();
-}
-
-template <typename AccT>
-cudaError_t launch_pass(int M, const PassDesc &d, bool adjoint, cudaStream_t st) {
-    switch (M) {
-    case 0: return launch_pass_t<0, AccT>(d, adjoint, st);
-    case 1: return launch_pass_t<1, AccT>(d, adjoint, st);
-    case 2: return launch_pass_t<2, AccT>(d, adjoint, st);
-    case 3: return launch_pass_t<3, AccT>(d, adjoint, st);
-    case 4: return launch_pass_t<4, AccT>(d, adjoint, st);
-    case 5: return launch_pass_t<5, AccT>(d, adjoint, st);
-    default: return launch_pass_t<6, AccT>(d, adjoint, st);
+// Pick the fused-kernel instantiation for the pass's element types. Shared
+// tiles of a first pass over a uint8 image hold level-3 values (<= 255*8) as
+// uint16.
+cudaError_t launch_forward(int M, const PassDesc &d, int acc, cudaStream_t st) {
+    const int src = d.lo.type, dst = d.hi.type;
+    if (acc == kF32) {
+        if (src == kU8) return launch_fused_f32_u8(M, d, st);
+        return launch_fused_f32_f32(M, d, st);
     }
+    if (src == kU8) {
+        if (dst == kU16) return launch_fused_i32_u8_u16(M, d, st);
+        return launch_fused_i32_u8_i32(M, d, st);
+    }
+    if (src == kU16) return launch_fused_i32_u16(M, d, st);
+    return launch_fused_i32_i32(M, d, st);
 }
 
-// Fill the pass descriptor shared by forward and adjoint: pass p of plan P.
+// Block-A warp-columns per tile: wider tiles compute less halo but need more
+// shared memory (fewer CTAs per SM). Overridable for tuning through
+// FHT_TUNE="n_a_u16,n_a_wide".
+struct Tune {
+    int n_a_u16 = 2;    // first pass over uint8 images (uint16 shared tile)
+    int n_a_wide = 1;   // 4-byte shared tiles
+    Tune() {
+        if (const char *e = getenv("FHT_TUNE")) {
+            int a = 0, b = 0;
+            if (sscanf(e, "%d,%d", &a, &b) == 2 && a >= 1 && a <= 3 && b >= 1 && b <= 3) {
+                n_a_u16 = a;
+                n_a_wide = b;
+            }
+        }
+    }
+};
+const Tune g_tune;
+
+// First passes over uint8 images keep their shared tile in uint16.
+bool acc_is_u16_mid(const QuadPlan &P, int p) { return p == 0 && P.in_elem == kU8 && P.acc_elem == kI32; }
+
 PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &final_side,
                    void *ws, const FinalMap &fm, int t_lo, int t_hi) {
     PassDesc d{};
@@ -258,8 +257,9 @@ PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &fina
     d.a_lo = t_lo >> drop;
     d.a_count = (t_hi >> drop) - d.a_lo + 1;
     d.s_count = P.n >> P.k[p + 1];
-    d.tile_w = tile_width(P.m[p]);
-    d.tiles = (d.hi.cols + d.tile_w - 1) / d.tile_w;
+    d.p_begin = 0;
+    d.p_count = d.hi.cols;
+    d.cyclic = P.adjoint ? 1 : 0;
     d.t_first = fm.t_first;
     d.t_last = fm.t_last;
     d.row_base = fm.row_base;
@@ -267,6 +267,8 @@ PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &fina
     d.shift_on = fm.shift_on;
     d.shift_inverse = fm.shift_inverse;
     d.shift_win = P.w_in;
+    d.black_wc = P.w_c;
+    d.n_a = P.m[p] >= 4 ? (acc_is_u16_mid(P, p) ? g_tune.n_a_u16 : g_tune.n_a_wide) : 1;
     return d;
 }
 
@@ -275,8 +277,7 @@ fht_status run_forward(const QuadPlan &P, const Side &image, const Side &out,
                        cudaStream_t st) {
     for (int p = 0; p < P.npass; ++p) {
         PassDesc d = pass_desc(P, p, image, out, ws, fm, t_lo, t_hi);
-        cudaError_t e = acc_elem == kF32 ? launch_pass<float>(P.m[p], d, false, st)
-                                         : launch_pass<int32_t>(P.m[p], d, false, st);
+        cudaError_t e = launch_forward(P.m[p], d, acc_elem, st);
         if (e != cudaSuccess) {
             g_last_cuda_error = (int)e;
             return FHT_ECUDA;
@@ -285,14 +286,36 @@ fht_status run_forward(const QuadPlan &P, const Side &image, const Side &out,
     return FHT_OK;
 }
 
+// Transpose of quadrant plan P (built with adjoint = true): the gradient's
+// rows t come from grad_hough through `fm`; the result is cropped to the
+// (transposed) image and written, or added, into grad_img.
 fht_status run_adjoint(const QuadPlan &P, const Side &grad_img, const Side &grad_hough,
                        const FinalMap &fm, int acc_elem, int accumulate, void *ws,
                        cudaStream_t st) {
-    for (int p = P.npass - 1; p >= 0; --p) {
-        PassDesc d = pass_desc(P, p, grad_img, grad_hough, ws, fm, 0, P.n - 1);
-        d.accumulate = accumulate;
-        cudaError_t e = acc_elem == kF32 ? launch_pass<float>(P.m[p], d, true, st)
-                                         : launch_pass<int32_t>(P.m[p], d, true, st);
+    for (int p = 0; p < P.npass; ++p) {
+        // output rows y < h_c of the opposite-sign transform are the image rows
+        PassDesc d = pass_desc(P, p, grad_hough, grad_img, ws, FinalMap{0, P.n - 1, 0, 1, 0, 0},
+                               0, P.h_c - 1);
+        if (p == 0) {
+            d.transpose = 0;
+            d.lo.cols = P.W;
+            d.src_t_first = fm.t_first;
+            d.src_t_last = fm.t_last;
+            d.src_row_base = fm.row_base;
+            d.src_row_dir = fm.row_dir;
+        }
+        if (d.hi_final) {
+            d.dst_image = 1;
+            d.dst_h = P.h_c;
+            d.dst_w = P.w_c;
+            d.dst_transpose = P.transpose;
+            d.accumulate = accumulate;
+            d.hi.cols = P.W;
+            // only columns X < w_c reach the image: p = X + sigma_plus * n
+            d.p_begin = P.sigma > 0 ? P.n : 0;
+            d.p_count = P.w_c;
+        }
+        cudaError_t e = launch_forward(P.m[p], d, acc_elem, st);
         if (e != cudaSuccess) {
             g_last_cuda_error = (int)e;
             return FHT_ECUDA;
@@ -432,12 +455,18 @@ fht_status fht_workspace_size(int h, int w, fht_layout layout, fht_quadrant q,
     int acc = acc_kind(in_t, acc_t);
     if (acc < 0) return FHT_EINVAL;
     size_t need = 0;
+    // the adjoint of an (acc, acc) transform runs full-width intermediates
+    const bool adj = in_t == acc_t;
     if (layout == FHT_LAYOUT_FULL) {
-        for (int qq = 0; qq < 4; ++qq)
+        for (int qq = 0; qq < 4; ++qq) {
             need = std::max(need, plan_workspace(make_plan(h, w, qq, true, elem_of(in_t), acc)));
+            if (adj)
+                need = std::max(need, plan_workspace(make_plan(h, w, qq, true, acc, acc, true)));
+        }
     } else if (layout == FHT_LAYOUT_QUADRANT) {
         if (!quadrant_ok(q)) return FHT_EINVAL;
         need = plan_workspace(make_plan(h, w, q, false, elem_of(in_t), acc));
+        if (adj) need = std::max(need, plan_workspace(make_plan(h, w, q, false, acc, acc, true)));
     } else {
         return FHT_EINVAL;
     }
@@ -563,7 +592,7 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
     cudaStream_t st = (cudaStream_t)stream;
     if (layout == FHT_LAYOUT_QUADRANT) {
         if (!quadrant_ok(q)) return FHT_EINVAL;
-        QuadPlan P = make_plan(h, w, q, false, acc, acc);
+        QuadPlan P = make_plan(h, w, q, false, acc, acc, true);
         if (P.K > kMaxK || in_pitch < P.W) return FHT_EINVAL;
         size_t need = plan_workspace(P);
         if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
@@ -577,7 +606,7 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
     QuadPlan plans[4];
     size_t need = 0;
     for (int qq = 0; qq < 4; ++qq) {
-        plans[qq] = make_plan(h, w, qq, true, acc, acc);
+        plans[qq] = make_plan(h, w, qq, true, acc, acc, true);
         need = std::max(need, plan_workspace(plans[qq]));
     }
     if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;

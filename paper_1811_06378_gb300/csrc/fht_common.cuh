@@ -46,12 +46,23 @@ struct PassDesc {
     int lo_image;    // lo is the level-0 image (zero outside rows x cols)
     int transpose;   // lo image is read transposed (quadrants Q2, Q3)
     int hi_final;    // hi is the final level: user layout (rows mapped, X columns)
-    int accumulate;  // adjoint into the image: add to what is there
     int n, W, K, k0, sigma;
+    // Adjoint passes (the opposite-sign transform of a gradient): every level
+    // spans all W columns, read cyclically; the level-0 source is the
+    // gradient, row t at src_row_base + src_row_dir*t for t in
+    // [src_t_first, src_t_last] and zero otherwise; the final level goes to the
+    // image gradient (rows < dst_h, columns < dst_w, transposed if
+    // dst_transpose, added to its contents if accumulate).
+    int cyclic;
+    int src_t_first, src_t_last, src_row_base, src_row_dir;
+    int dst_image, dst_h, dst_w, dst_transpose, accumulate;
+    int p_begin, p_count;  // destination columns [p_begin, p_begin + p_count) are tiled
     int a_lo, a_count;   // level-k0 slopes of the groups (range pruning)
     int s_count;         // strips at level k1
     int tile_w;          // output columns per tile
     int tiles;           // tiles per group
+    int n_a;             // fused kernel: block-A warp-columns per tile
+    int black_wc;        // content width w_c (black-zone test of the final level)
     // final level only: slope t is row row_base + row_dir*t of the output,
     // present for t in [t_first, t_last]
     int t_first, t_last, row_base, row_dir;

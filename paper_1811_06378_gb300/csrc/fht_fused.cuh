@@ -1,0 +1,628 @@
+// fht_fused.cuh -- register-level butterfly pass (forward) for sm_103a.
+//
+// One CTA computes one (group, tile) of a pass of m = MA + MB levels
+// (see fht_common.cuh for groups, the pass identity and compact columns).
+// Inside the tile, columns run in the direction of the shifts ("buffer
+// coordinates"), so both signs use one butterfly.
+//
+// Data placement:
+//  * a lane owns kV = 8 consecutive buffer columns of 2^MA (or 2^MB) rows in
+//    registers; a level's shift reaches at most 4 columns into lane+1's
+//    registers, fetched with warp shuffles. A warp therefore produces valid
+//    results for lanes 0..30 (248 columns); warps overlap by one lane.
+//  * block A (levels 0..MA): rows g*2^MA + rho of the group's 2^m sheared
+//    source rows, loaded straight from global memory with 8/16-byte vectors
+//    and realigned in registers without branches; results go to a shared tile.
+//  * block B (levels MA..m): rows g*2^MA + a' (g < 2^MB) read from the tile
+//    with the local shear a'*g (the pass identity applied inside the pass),
+//    stored to global memory through the destination map.
+//  * the shared tile is padded by one 4-byte word (or two 2-byte elements) per
+//    8 columns: lanes 8 columns apart then sit 9 words (5 words) apart, so
+//    block A's stores and block B's sheared loads are bank-conflict-free and
+//    use immediate offsets from one base address per row.
+#pragma once
+
+#include <type_traits>
+
+#include "fht_kernels.cuh"
+
+namespace fht {
+
+constexpr int kV = 8;                         // columns per lane
+constexpr int kLanesValid = 31;               // lanes whose results are complete
+constexpr int kWarpValid = kV * kLanesValid;  // 248 columns per warp
+
+template <typename T>
+__device__ __forceinline__ T shfl_next(T v) {
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+
+// ------------------------------------------------------------ shared tile
+
+template <typename MidE>
+struct TilePad {
+    static constexpr int kPad = sizeof(MidE) == 2 ? 2 : 1;   // elements per 8 columns
+};
+
+__host__ __device__ inline int tile_pos(int x, int pad) { return x + pad * (x >> 3); }
+
+// ------------------------------------------------------------ global row segments
+
+__device__ __forceinline__ uint32_t sel4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, int j) {
+    uint32_t lo = (j & 1) ? b : a;
+    uint32_t hi = (j & 1) ? d : c;
+    return (j & 2) ? hi : lo;
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc from_word(uint32_t w, std::true_type /*float*/) {
+    return __uint_as_float(w);
+}
+template <typename Acc>
+__device__ __forceinline__ Acc from_word(uint32_t w, std::false_type) {
+    return (Acc)(int32_t)w;
+}
+
+// v[k] = row[lo + k] for k < 8, zero outside [0, cols). Fast path: the aligned
+// granules covering the 8 elements are loaded whole; the start offset inside
+// the first granule selects the elements with selects and byte permutes.
+template <typename E, typename Acc>
+__device__ __forceinline__ void load8(const E *row, int lo, int cols, Acc (&v)[kV]) {
+    if (lo >= 0 && lo + kV <= cols) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(row + lo);
+        if constexpr (sizeof(E) == 1) {
+            const int delta = (int)(a & 7);
+            const uint2 *g = reinterpret_cast<const uint2 *>(a & ~(uintptr_t)7);
+            uint2 q0 = __ldg(g), q1 = make_uint2(0, 0);
+            if (delta) q1 = __ldg(g + 1);
+            const uint32_t w0 = q0.x, w1 = q0.y, w2 = q1.x, w3 = q1.y;
+            const bool hi = delta >= 4;
+            const uint32_t u0 = hi ? w1 : w0, u1 = hi ? w2 : w1, u2 = hi ? w3 : w2;
+            const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)(delta & 3);
+            const uint32_t b0 = __byte_perm(u0, u1, sel), b1 = __byte_perm(u1, u2, sel);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[k] = (Acc)(int32_t)((b0 >> (8 * k)) & 0xffu);
+                v[k + 4] = (Acc)(int32_t)((b1 >> (8 * k)) & 0xffu);
+            }
+        } else if constexpr (sizeof(E) == 2) {
+            const int delta = (int)((a & 15) >> 1);
+            const uint4 *g = reinterpret_cast<const uint4 *>(a & ~(uintptr_t)15);
+            uint4 q0 = __ldg(g), q1 = make_uint4(0, 0, 0, 0);
+            if (delta) q1 = __ldg(g + 1);
+            const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+            const int j = delta >> 1;
+            uint32_t u[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) u[i] = sel4(w[i], w[i + 1 < 8 ? i + 1 : 7],
+                                                  w[i + 2 < 8 ? i + 2 : 7], w[i + 3 < 8 ? i + 3 : 7], j);
+            const uint32_t sel = (delta & 1) ? 0x5432u : 0x3210u;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t pr = __byte_perm(u[i], u[i + 1], sel);
+                v[2 * i] = (Acc)(int32_t)(pr & 0xffffu);
+                v[2 * i + 1] = (Acc)(int32_t)(pr >> 16);
+            }
+        } else {
+            const int delta = (int)((a & 15) >> 2);
+            const uint4 *g = reinterpret_cast<const uint4 *>(a & ~(uintptr_t)15);
+            uint4 q0 = __ldg(g), q1 = __ldg(g + 1), q2 = make_uint4(0, 0, 0, 0);
+            if (delta) q2 = __ldg(g + 2);
+            const uint32_t w[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y,
+                                    q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+            using IsF = std::integral_constant<bool, std::is_same<Acc, float>::value &&
+                                                         std::is_same<E, float>::value>;
+#pragma unroll
+            for (int k = 0; k < kV; ++k)
+                v[k] = from_word<Acc>(sel4(w[k], w[k + 1], w[k + 2], w[k + 3], delta), IsF());
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kV; ++k) {
+            const int c = lo + k;
+            v[k] = (c >= 0 && c < cols) ? (Acc)row[c] : Acc(0);
+        }
+    }
+}
+
+// Cyclic variant: v[k] = row[(lo + k) mod W] (gradients have no zero zone).
+template <typename E, typename Acc>
+__device__ __forceinline__ void load8_cyclic(const E *row, int lo, int W, Acc (&v)[kV]) {
+    int c = lo;
+    if (c < 0 || c >= W) {
+        c %= W;
+        if (c < 0) c += W;
+    }
+    if (c + kV <= W) {
+        load8<E, Acc>(row, c, W, v);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        int x = c + k;
+        if (x >= W) x -= W;
+        if (x >= W) x %= W;
+        v[k] = (Acc)row[x];
+    }
+}
+
+template <typename Acc>
+__device__ __forceinline__ void reverse8(Acc (&v)[kV]) {
+#pragma unroll
+    for (int k = 0; k < kV / 2; ++k) {
+        Acc t = v[k];
+        v[k] = v[kV - 1 - k];
+        v[kV - 1 - k] = t;
+    }
+}
+
+// Store 8 ascending elements at row[lo..lo+7], dropping those outside [0, cols).
+template <typename E, typename Acc>
+__device__ __forceinline__ void store8(E *row, int lo, int cols, const Acc (&v)[kV]) {
+    E *p = row + lo;
+    if (lo >= 0 && lo + kV <= cols && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        if constexpr (sizeof(E) == 2) {
+            uint4 q;
+            q.x = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
+            q.y = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
+            q.z = (uint32_t)(uint16_t)v[4] | ((uint32_t)(uint16_t)v[5] << 16);
+            q.w = (uint32_t)(uint16_t)v[6] | ((uint32_t)(uint16_t)v[7] << 16);
+            *reinterpret_cast<uint4 *>(p) = q;
+        } else {
+            using V4 = typename std::conditional<std::is_same<E, float>::value, float4, int4>::type;
+            V4 a, b;
+            a.x = (E)v[0]; a.y = (E)v[1]; a.z = (E)v[2]; a.w = (E)v[3];
+            b.x = (E)v[4]; b.y = (E)v[5]; b.z = (E)v[6]; b.w = (E)v[7];
+            reinterpret_cast<V4 *>(p)[0] = a;
+            reinterpret_cast<V4 *>(p)[1] = b;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kV; ++k) {
+            const int c = lo + k;
+            if (c >= 0 && c < cols) row[c] = (E)v[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------ register butterfly
+
+// MR levels on 2^MR rows x 8 columns held by this lane; a bottom row's shifted
+// columns past this lane's 8 come from lane+1 (lane 31 receives lane 0's,
+// which only ever reaches lane 31's own discarded results).
+template <int MR, typename Acc>
+__device__ __forceinline__ void reg_butterfly(Acc (&v)[1 << MR][kV]) {
+    constexpr int R = 1 << MR;
+#pragma unroll
+    for (int half = 1; half < R; half *= 2) {
+        Acc nv[R][kV];
+#pragma unroll
+        for (int s0 = 0; s0 < R; s0 += 2 * half) {
+#pragma unroll
+            for (int u = 0; u < half; ++u) {
+                const Acc *top = v[s0 + u];
+                const Acc *bot = v[s0 + half + u];
+                Acc nb[kV];
+#pragma unroll
+                for (int k = 0; k < kV; ++k) nb[k] = k <= u ? shfl_next(bot[k]) : Acc(0);
+#pragma unroll
+                for (int k = 0; k < kV; ++k) {
+                    Acc b0 = k + u < kV ? bot[k + u] : nb[k + u - kV];
+                    Acc b1 = k + u + 1 < kV ? bot[k + u + 1] : nb[k + u + 1 - kV];
+                    nv[s0 + 2 * u][k] = Arith<Acc>::add(top[k], b0);
+                    nv[s0 + 2 * u + 1][k] = Arith<Acc>::add(top[k], b1);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k = 0; k < kV; ++k) v[r][k] = nv[r][k];
+    }
+}
+
+// ------------------------------------------------------------ pass geometry
+
+// Tile geometry of a pass with levels MA + MB (host and device agree on it).
+struct TileGeom {
+    int tile_out;    // output columns per tile
+    int n_a, n_b;    // warp-columns of blocks A and B
+    int cols;        // tile columns block B may read
+    int pitch;       // shared-memory row pitch (elements, padded), 0 if no tile
+};
+
+__host__ __device__ inline TileGeom tile_geom(int MA, int MB, int n_a, int nwarps, int pad) {
+    TileGeom g{};
+    if (MB == 0) {
+        g.n_a = nwarps;
+        g.tile_out = nwarps * kWarpValid;
+        return g;
+    }
+    const int RA = 1 << MA, RB = 1 << MB;
+    // block B's last valid lane reaches (RB-1) + (RA-1)(RB-1) columns past the
+    // tile: those must lie inside block A's valid columns
+    const int reach = (RB - 1) * RA;
+    g.n_a = n_a;
+    g.tile_out = (n_a * kWarpValid - reach) / kV * kV;
+    g.n_b = (g.tile_out + kWarpValid - 1) / kWarpValid;
+    // highest column block B loads (+1), lane 31 included, plus one granule
+    const int max_col = (g.n_b - 1) * kWarpValid + 32 * kV + (RA - 1) * (RB - 1) + kV;
+    g.cols = (max_col > n_a * kWarpValid ? max_col : n_a * kWarpValid + kV);
+    g.cols = (g.cols + 7) & ~7;
+    g.pitch = (tile_pos(g.cols, pad) + 7) & ~7;
+    return g;
+}
+
+// ------------------------------------------------------------ the pass item
+
+// Source row segment for block A: 8 buffer columns starting at i0 of buffer
+// row s, into v (buffer order).
+template <typename Acc, typename SrcE>
+__device__ __forceinline__ void load_source(const PassDesc &d, int M, int S, int a, int s,
+                                            int A_off, int i0, Acc (&v)[kV]) {
+    const int sg = d.sigma;
+    const int p_first = A_off + sg * (i0 + a * s);
+    const int lo = sg > 0 ? p_first : p_first - (kV - 1);
+    const SrcE *base = reinterpret_cast<const SrcE *>(d.lo.ptr);
+    if (d.lo_image) {
+        int row = S * (1 << M) + s;
+        const int col = lo - (sg > 0 ? 1 : 0);
+        if (d.cyclic) {
+            // gradient rows through the layout's row map
+            if (row < d.src_t_first || row > d.src_t_last) {
+#pragma unroll
+                for (int k = 0; k < kV; ++k) v[k] = Acc(0);
+                return;
+            }
+            row = d.src_row_base + d.src_row_dir * row;
+            load8_cyclic<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, col, d.W, v);
+        } else {
+            if (row >= d.lo.rows) {
+#pragma unroll
+                for (int k = 0; k < kV; ++k) v[k] = Acc(0);
+                return;
+            }
+            load8<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, col, d.lo.cols, v);
+        }
+    } else {
+        const int row = ((S * (1 << M) + s) << d.k0) + a;
+        if (d.cyclic) load8_cyclic<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, lo, d.W, v);
+        else load8<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, lo, d.lo.cols, v);
+    }
+    if (sg < 0) reverse8(v);
+}
+
+// Transposed image block for block A of the first pass (quadrants Q2, Q3):
+// rows s0..s0+RA-1 of the transposed image are image columns; the 8 buffer
+// columns are 8 image rows.
+template <int RA, typename Acc, typename SrcE>
+__device__ __forceinline__ void load_source_transposed(const PassDesc &d, int M, int S,
+                                                       int s0, int A_off, int i0,
+                                                       Acc (&v)[RA][kV]) {
+    const int sg = d.sigma;
+    const int p_first = A_off + sg * i0;
+    const int lo = (sg > 0 ? p_first : p_first - (kV - 1)) - (sg > 0 ? 1 : 0);  // image row
+    const int y0 = S * (1 << M) + s0;                                         // image column
+    const SrcE *img = reinterpret_cast<const SrcE *>(d.lo.ptr);
+    Acc blk[kV][kV];   // blk[k][j]: image row lo + k, image column y0 + j
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        const int c = lo + k;   // image row
+        if (c >= 0 && c < d.lo.cols) {
+            load8<SrcE, Acc>(img + (int64_t)c * d.lo.pitch, y0, d.lo.rows, blk[k]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kV; ++j) blk[k][j] = Acc(0);
+        }
+    }
+    // buffer order: ascending image rows for sigma = +1, descending otherwise
+#pragma unroll
+    for (int r = 0; r < RA; ++r)
+#pragma unroll
+        for (int k = 0; k < kV; ++k) v[r][k] = sg > 0 ? blk[k][r] : blk[kV - 1 - k][r];
+}
+
+// Destination of one lane's 8 buffer columns (i0..i0+7): everything that does
+// not depend on the row is computed once per item.
+struct DestCols {
+    int lo;       // lowest destination column p of the 8
+    int X0;       // final level without fhtshift: output column of p = lo
+    bool vec;     // the 8 land contiguously, in bounds and 16-byte aligned
+};
+
+template <typename Acc, typename DstE>
+__device__ __forceinline__ DestCols dest_cols(const PassDesc &d, int D, int i0) {
+    DestCols c;
+    const int sg = d.sigma;
+    const int p_first = D + sg * i0;
+    c.lo = sg > 0 ? p_first : p_first - (kV - 1);
+    if (!d.hi_final) {
+        c.X0 = c.lo;
+        c.vec = c.lo >= 0 && c.lo + kV <= d.hi.cols && (d.hi.pitch & 7) == 0 &&
+                (c.lo & 7) == 0 && ((reinterpret_cast<uintptr_t>(d.hi.ptr) & 15) == 0);
+        return c;
+    }
+    // column of p: X = p - sigma_plus*n (mod W); fhtshift handled per row
+    int X0 = c.lo - (sg > 0 ? d.n : 0);
+    if (X0 < 0) X0 += d.W;
+    c.X0 = X0;
+    c.vec = !d.shift_on && c.lo >= 0 && c.lo + kV <= d.W && X0 + kV <= d.W && (X0 & 3) == 0 &&
+            (d.hi.pitch & 3) == 0 && ((reinterpret_cast<uintptr_t>(d.hi.ptr) & 15) == 0);
+    return c;
+}
+
+// Store 8 buffer columns of level-k1 row hi_r (values in buffer order).
+template <typename Acc, typename DstE>
+__device__ __forceinline__ void store_dest(const PassDesc &d, const DestCols &c, int hi_r,
+                                           const Acc (&v)[kV]) {
+    const int sg = d.sigma;
+    Acc asc[kV];
+#pragma unroll
+    for (int k = 0; k < kV; ++k) asc[k] = sg > 0 ? v[k] : v[kV - 1 - k];
+    DstE *base = reinterpret_cast<DstE *>(d.hi.ptr);
+    if (!d.hi_final) {
+        DstE *row = base + (int64_t)hi_r * d.hi.pitch;
+        if (c.vec) store8<DstE, Acc>(row, c.lo, c.lo + kV, asc);
+        else store8<DstE, Acc>(row, c.lo, d.hi.cols, asc);
+        return;
+    }
+    const int t = hi_r;
+    if (t < d.t_first || t > d.t_last) return;
+    DstE *row = base + ((int64_t)d.row_base + (int64_t)d.row_dir * t) * d.hi.pitch;
+    if (c.vec) {
+        store8<DstE, Acc>(row, c.X0, c.X0 + kV, asc);
+        return;
+    }
+    const int W = d.W;
+    int off = sg > 0 ? -d.n : 0;
+    if (d.shift_on) {
+        const int s = fhtshift_amount(t, W, d.shift_win, sg);
+        off += d.shift_inverse ? -s : s;
+    }
+    while (off < 0) off += W;
+    while (off >= W) off -= W;
+    const int lo = c.lo;
+    int X0 = lo + off;
+    if (X0 >= W) X0 -= W;
+    if (lo >= 0 && lo + kV <= W && X0 >= 0 && X0 + kV <= W) {
+        store8<DstE, Acc>(row, X0, W, asc);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kV; ++k) {
+            const int p = lo + k;
+            if (p >= 0 && p < W) {
+                int X = p + off;
+                if (X >= W) X -= W;
+                row[X] = (DstE)asc[k];
+            }
+        }
+    }
+}
+
+// Final level of an adjoint: R consecutive output rows y0.. (image rows of the
+// (transposed) image) x this lane's 8 columns go to the image gradient,
+// cropped to dst_h x dst_w, transposed for the horizontal quadrants, added to
+// the gradient already there when accumulating.
+template <typename E, typename Acc>
+__device__ __forceinline__ E acc_store(E old, Acc v, bool acc) {
+    return acc ? (E)Arith<Acc>::add((Acc)old, v) : (E)v;
+}
+
+template <int R, typename Acc, typename DstE>
+__device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int lo,
+                                                  const Acc (&v)[R][kV]) {
+    // columns p in [p_begin, p_begin + p_count) are exactly the image columns
+    // X = p - sigma_plus*n < dst_w; a tile wider than W would otherwise reach
+    // the same X again through the cyclic wrap
+    const int sg = d.sigma;
+    const bool acc = d.accumulate != 0;
+    const int p_lo = d.p_begin, p_hi = d.p_begin + d.p_count;
+    const int X0 = lo - (sg > 0 ? d.n : 0);   // column of p = lo (valid when lo >= p_lo)
+    DstE *img = reinterpret_cast<DstE *>(d.hi.ptr);
+    const int64_t pitch = d.hi.pitch;
+    const bool inside = lo >= p_lo && lo + kV <= p_hi;
+    if (!d.dst_transpose) {
+        const bool vec = inside && (X0 & 3) == 0 && (pitch & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(img) & 15) == 0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = y0 + r;
+            if (y >= d.dst_h) continue;
+            DstE *row = img + (int64_t)y * pitch;
+            Acc asc[kV];
+#pragma unroll
+            for (int k = 0; k < kV; ++k) asc[k] = sg > 0 ? v[r][k] : v[r][kV - 1 - k];
+            if (vec) {
+                if (acc) {
+                    Acc old[kV];
+                    load8<DstE, Acc>(row, X0, X0 + kV, old);
+#pragma unroll
+                    for (int k = 0; k < kV; ++k) asc[k] = Arith<Acc>::add(old[k], asc[k]);
+                }
+                store8<DstE, Acc>(row, X0, X0 + kV, asc);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kV; ++k) {
+                    const int p = lo + k;
+                    if (p >= p_lo && p < p_hi)
+                        row[X0 + k] = acc_store<DstE, Acc>(row[X0 + k], asc[k], acc);
+                }
+            }
+        }
+        return;
+    }
+    // transposed: image row X, image columns y0 .. y0 + R - 1
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        const int p = lo + k;
+        if (p < p_lo || p >= p_hi) continue;
+        const int X = X0 + k;
+        Acc col[R];   // column k in ascending p order (selects, no dynamic indexing)
+#pragma unroll
+        for (int r = 0; r < R; ++r) col[r] = sg > 0 ? v[r][k] : v[r][kV - 1 - k];
+        DstE *row = img + (int64_t)X * pitch;
+        if constexpr (R >= 4) {
+            DstE *q4 = row + y0;
+            if (y0 + R <= d.dst_h && (reinterpret_cast<uintptr_t>(q4) & 15) == 0) {
+                using V4 = typename std::conditional<std::is_same<DstE, float>::value, float4,
+                                                     int4>::type;
+#pragma unroll
+                for (int j = 0; j < R / 4; ++j) {
+                    V4 q;
+                    if (acc) q = reinterpret_cast<const V4 *>(q4)[j];
+                    else q.x = q.y = q.z = q.w = DstE(0);
+                    q.x = acc_store<DstE, Acc>(q.x, col[4 * j + 0], acc);
+                    q.y = acc_store<DstE, Acc>(q.y, col[4 * j + 1], acc);
+                    q.z = acc_store<DstE, Acc>(q.z, col[4 * j + 2], acc);
+                    q.w = acc_store<DstE, Acc>(q.w, col[4 * j + 3], acc);
+                    reinterpret_cast<V4 *>(q4)[j] = q;
+                }
+                continue;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int y = y0 + r;
+            if (y < d.dst_h) row[y] = acc_store<DstE, Acc>(row[y], col[r], acc);
+        }
+    }
+}
+
+// Is the whole tile inside the black zone of every slope of the group?
+// (final level only: slopes t in [a*2^M, a*2^M + 2^M - 1])
+__device__ __forceinline__ bool tile_all_black(const PassDesc &d, int M, int a, int p0,
+                                               int tile_out) {
+    if (!d.hi_final || d.cyclic) return false;
+    const int t_max = (a << M) + (1 << M) - 1;
+    const int lo = p0, hi = p0 + tile_out;   // [lo, hi) in p
+    if (d.sigma > 0) {
+        // zero for p in [0, n - t) and p in [w_c + n, W)
+        return hi <= d.n - t_max || lo >= d.black_wc + d.n;
+    }
+    // sigma = -1: zero for p in [w_c + t, W)
+    return lo >= d.black_wc + t_max;
+}
+
+template <int MA, int MB, typename Acc, typename SrcE, typename MidE, typename DstE>
+__device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm) {
+    constexpr int M = MA + MB, RA = 1 << MA, RB = 1 << MB;
+    constexpr int PAD = TilePad<MidE>::kPad;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const TileGeom G = tile_geom(MA, MB, d.n_a, nwarps, PAD);
+    const int T = G.tile_out;
+    const int S = gy / d.a_count, a = d.a_lo + gy % d.a_count;
+    const int p0 = d.p_begin + tile * T;
+    const int sg = d.sigma;
+    const int A_off = sg > 0 ? p0 - (1 << (d.k0 + M)) + (1 << d.k0) : p0 + T - 1;
+    const int D = sg > 0 ? p0 : p0 + T - 1;
+    const bool black = tile_all_black(d, M, a, p0, T);
+
+    if constexpr (MB == 0) {
+        // single register block: source -> registers -> destination
+        for (int item = warp; item < G.n_a; item += nwarps) {
+            const int i0 = item * kWarpValid + lane * kV;
+            Acc v[RA][kV];
+            if (!black) {
+                if (d.lo_image && d.transpose) {
+                    load_source_transposed<RA, Acc, SrcE>(d, M, S, 0, A_off, i0, v);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RA; ++r)
+                        load_source<Acc, SrcE>(d, M, S, a, r, A_off, i0, v[r]);
+                }
+                reg_butterfly<MA, Acc>(v);
+            } else {
+#pragma unroll
+                for (int r = 0; r < RA; ++r)
+#pragma unroll
+                    for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
+            }
+            if (lane < kLanesValid && i0 < T) {
+                const DestCols dc = dest_cols<Acc, DstE>(d, D, i0);
+                if (d.dst_image) {
+                    store_image_block<RA, Acc, DstE>(d, hi_row(d, M, S, a, 0), dc.lo, v);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < RA; ++c)
+                        store_dest<Acc, DstE>(d, dc, hi_row(d, M, S, a, c), v[c]);
+                }
+            }
+        }
+        return;
+    } else {
+        const int P = G.pitch;
+        if (!black) {
+            // block A: mini-strip g (rows g*RA + rho), warp-column wc
+            for (int item = warp; item < RB * G.n_a; item += nwarps) {
+                const int g = item % RB, wc = item / RB;
+                const int i0 = wc * kWarpValid + lane * kV;
+                Acc v[RA][kV];
+                if (d.lo_image && d.transpose) {
+                    load_source_transposed<RA, Acc, SrcE>(d, M, S, g * RA, A_off, i0, v);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RA; ++r)
+                        load_source<Acc, SrcE>(d, M, S, a, g * RA + r, A_off, i0, v[r]);
+                }
+                reg_butterfly<MA, Acc>(v);
+                if (lane < kLanesValid) {
+                    const int pos = (8 + PAD) * (i0 >> 3);   // i0 is a multiple of 8
+#pragma unroll
+                    for (int c = 0; c < RA; ++c) {
+                        MidE *row = sm + (g * RA + c) * P + pos;
+                        if constexpr (PAD == 2) {
+                            uint32_t *w = reinterpret_cast<uint32_t *>(row);
+#pragma unroll
+                            for (int k = 0; k < kV / 2; ++k)
+                                w[k] = (uint32_t)(uint16_t)v[c][2 * k] |
+                                       ((uint32_t)(uint16_t)v[c][2 * k + 1] << 16);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < kV; ++k) row[k] = (MidE)v[c][k];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // block B: level-MA slope a2 of every mini-strip g, sheared by a2*g
+        for (int item = warp; item < RA * G.n_b; item += nwarps) {
+            const int a2 = item % RA, jc = item / RA;
+            const int i0 = jc * kWarpValid + lane * kV;
+            Acc v[RB][kV];
+            if (!black) {
+#pragma unroll
+                for (int g = 0; g < RB; ++g) {
+                    const int x0 = i0 + a2 * g;
+                    const int delta = x0 & 7;
+                    const MidE *row = sm + (g * RA + a2) * P + tile_pos(x0, PAD);
+                    MidE raw[kV + PAD];
+#pragma unroll
+                    for (int j = 0; j < kV + PAD; ++j) raw[j] = row[j];
+#pragma unroll
+                    for (int k = 0; k < kV; ++k)
+                        v[g][k] = (Acc)(k + delta >= kV ? raw[k + PAD] : raw[k]);
+                }
+                reg_butterfly<MB, Acc>(v);
+            } else {
+#pragma unroll
+                for (int r = 0; r < RB; ++r)
+#pragma unroll
+                    for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
+            }
+            if (lane < kLanesValid && i0 < T) {
+                const DestCols dc = dest_cols<Acc, DstE>(d, D, i0);
+                if (d.dst_image) {
+                    store_image_block<RB, Acc, DstE>(d, hi_row(d, M, S, a, a2 * RB), dc.lo, v);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < RB; ++c)
+                        store_dest<Acc, DstE>(d, dc, hi_row(d, M, S, a, a2 * RB + c), v[c]);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace fht

@@ -1,0 +1,42 @@
+// fht_host.h -- host-side declarations shared by the library's translation
+// units: launch accounting and the per-type fused-pass launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "fht_common.cuh"
+
+namespace fht {
+
+// Counts a kernel launch and, while profiling is on (fht_profile_begin),
+// brackets it with CUDA events on its stream: construct right before the
+// launch, call done() right after it.
+class LaunchScope {
+  public:
+    LaunchScope(const char *name, cudaStream_t st);
+    void done();
+
+  private:
+    cudaStream_t st_;
+    bool on_ = false;
+    std::string name_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+template <typename T> inline const char *acc_name();
+template <> inline const char *acc_name<float>() { return "f32"; }
+template <> inline const char *acc_name<int32_t>() { return "i32"; }
+
+// Fused forward pass of M levels, one launcher per (accumulator, source,
+// destination) element-type combination; each lives in its own translation
+// unit so the instantiations compile in parallel.
+cudaError_t launch_fused_i32_u8_u16(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_fused_i32_u8_i32(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_fused_i32_u16(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_fused_i32_i32(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_fused_f32_u8(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_fused_f32_f32(int M, const PassDesc &d, cudaStream_t st);
+
+}  // namespace fht

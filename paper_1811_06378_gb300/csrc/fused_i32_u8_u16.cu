@@ -1,0 +1,9 @@
+// fused_i32_u8_u16.cu -- fused forward pass instantiations: accumulator int32_t,
+// source uint8_t, shared tile uint16_t, destination uint16_t.
+#include "fht_fused_launch.cuh"
+
+namespace fht {
+cudaError_t launch_fused_i32_u8_u16(int M, const PassDesc &d, cudaStream_t st) {
+    return launch_fused_m<int32_t, uint8_t, uint16_t, uint16_t>(M, d, st);
+}
+}  // namespace fht
