@@ -156,6 +156,29 @@ fht_status fhtshift(const void *in, void *out, fht_dtype dtype, int h, int w,
                     fht_layout layout, fht_quadrant q, int inverse, int64_t in_pitch,
                     int64_t out_pitch, void *stream);
 
+/* fht_forward for callers that cannot allocate device memory. The paper has
+ * no counterpart; this is a property of the library, not of the method.
+ * Some callers cannot call cudaMalloc or anything that allocates: code that
+ * runs while a CUDA graph is being captured, code confined to a memory pool
+ * or budget it does not own, plugin hosts that forbid allocation after start-
+ * up. This entry point computes exactly what fht_forward computes (same
+ * arguments, minus the workspace) but keeps the intermediate butterfly levels
+ * in a fixed 64 MiB device array inside the library, which every GPU that
+ * loads the library holds until the process exits. It allocates nothing.
+ *
+ * Limit: requests for which fht_workspace_size(h, w, FHT_LAYOUT_QUADRANT, q,
+ * in_t, acc_t) exceeds 64 MiB return FHT_ENOMEM and enqueue nothing (a uint8
+ * image up to 4096 x 4096 into int32 fits).
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.
+ * Sharing: all calls on a device share the one array, which keeps the last
+ * call's contents (nothing in it needs to start at zero). Calls whose kernels
+ * overlap on the GPU race on it: issue them in order on one stream. */
+fht_status fht_forward_static(const void *img, fht_dtype in_t, int h, int w,
+                              int64_t in_pitch, fht_quadrant q, void *out,
+                              fht_dtype acc_t, int64_t out_pitch, void *stream);
+
 /* ------------------------------------------------------------------ adjoint */
 
 /* Adjoint (transpose) of fht_forward (layout QUADRANT, quadrant q) or of

@@ -1,0 +1,69 @@
+// fht_static.cu -- fht_forward_static: the single-quadrant forward transform
+// for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc, or any routine that allocates: code
+// that runs while a CUDA graph is being captured (allocation is not a
+// capturable operation), code running under an allocator or memory pool it
+// does not own (a framework's caching allocator, a real-time path with a
+// fixed memory budget), or a plugin host that forbids allocation after start-
+// up. fht_forward needs scratch for its intermediate butterfly levels, which
+// its caller must allocate. This entry point instead keeps that scratch in a
+// fixed device array defined in this file: the library allocates nothing at
+// call time, and every GPU that loads the library holds the array until the
+// process exits.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/fht.h"
+
+namespace {
+
+// The fixed scratch: 64 MiB, enough for a uint8 -> int32 quadrant of a
+// 4096 x 4096 image (its one intermediate level takes 34 MB as uint16).
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_ptr[kMaxDevices] = {};   // device address of the array, per device
+
+// Device address of the scratch on the current device. In host code the
+// array's name is only a stand-in, so the address comes from
+// cudaGetSymbolAddress, once per device, with that device current.
+fht_status scratch_on_current_device(void **ptr) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return FHT_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();   // do not leave this error for the caller's next check
+            return FHT_ECUDA;
+        }
+        g_scratch_ptr[dev] = p;
+    }
+    *ptr = g_scratch_ptr[dev];
+    return FHT_OK;
+}
+
+}  // namespace
+
+extern "C" fht_status fht_forward_static(const void *img, fht_dtype in_t, int h, int w,
+                                         int64_t in_pitch, fht_quadrant q, void *out,
+                                         fht_dtype acc_t, int64_t out_pitch, void *stream) {
+    size_t need = 0;
+    fht_status s = fht_workspace_size(h, w, FHT_LAYOUT_QUADRANT, q, in_t, acc_t, &need);
+    if (s != FHT_OK) return s;
+    if (need > kStaticScratchBytes) return FHT_ENOMEM;   // beyond the fixed maximum
+    void *scratch = nullptr;
+    if (need > 0) {
+        s = scratch_on_current_device(&scratch);
+        if (s != FHT_OK) return s;
+    }
+    // Nothing in the scratch needs to start at zero: every intermediate
+    // element the forward transform reads was written earlier in the same call.
+    return fht_forward(img, in_t, h, w, in_pitch, q, out, acc_t, out_pitch, scratch,
+                       need > 0 ? kStaticScratchBytes : 0, stream);
+}
