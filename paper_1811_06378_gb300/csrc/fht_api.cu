@@ -315,7 +315,8 @@ fht_status run_adjoint(const QuadPlan &P, const Side &grad_img, const Side &grad
             d.p_begin = P.sigma > 0 ? P.n : 0;
             d.p_count = P.w_c;
         }
-        cudaError_t e = launch_forward(P.m[p], d, acc_elem, st);
+        cudaError_t e = acc_elem == kF32 ? launch_adjoint_f32(P.m[p], d, st)
+                                         : launch_adjoint_i32(P.m[p], d, st);
         if (e != cudaSuccess) {
             g_last_cuda_error = (int)e;
             return FHT_ECUDA;

@@ -63,6 +63,34 @@ __device__ __forceinline__ Acc from_word(uint32_t w, std::false_type) {
     return (Acc)(int32_t)w;
 }
 
+// Eight values passed by value to and from the out-of-line edge paths.
+template <typename Acc>
+struct Vec8 {
+    Acc x[8];
+};
+
+// Edge paths (tile borders, wraps, unaligned rows) are rare; keeping them out
+// of line keeps the hot loop small enough for the instruction cache.
+template <typename E, typename Acc>
+__device__ __noinline__ Vec8<Acc> load8_edge(const E *row, int lo, int cols) {
+    Vec8<Acc> r;
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        const int c = lo + k;
+        r.x[k] = (c >= 0 && c < cols) ? (Acc)row[c] : Acc(0);
+    }
+    return r;
+}
+
+template <typename E, typename Acc>
+__device__ __noinline__ void store8_edge(E *row, int lo, int cols, Vec8<Acc> v) {
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        const int c = lo + k;
+        if (c >= 0 && c < cols) row[c] = (E)v.x[k];
+    }
+}
+
 // v[k] = row[lo + k] for k < 8, zero outside [0, cols). Fast path: the aligned
 // granules covering the 8 elements are loaded whole; the start offset inside
 // the first granule selects the elements with selects and byte permutes.
@@ -117,11 +145,9 @@ __device__ __forceinline__ void load8(const E *row, int lo, int cols, Acc (&v)[k
                 v[k] = from_word<Acc>(sel4(w[k], w[k + 1], w[k + 2], w[k + 3], delta), IsF());
         }
     } else {
+        const Vec8<Acc> r = load8_edge<E, Acc>(row, lo, cols);
 #pragma unroll
-        for (int k = 0; k < kV; ++k) {
-            const int c = lo + k;
-            v[k] = (c >= 0 && c < cols) ? (Acc)row[c] : Acc(0);
-        }
+        for (int k = 0; k < kV; ++k) v[k] = r.x[k];
     }
 }
 
@@ -177,11 +203,10 @@ __device__ __forceinline__ void store8(E *row, int lo, int cols, const Acc (&v)[
             reinterpret_cast<V4 *>(p)[1] = b;
         }
     } else {
+        Vec8<Acc> r;
 #pragma unroll
-        for (int k = 0; k < kV; ++k) {
-            const int c = lo + k;
-            if (c >= 0 && c < cols) row[c] = (E)v[k];
-        }
+        for (int k = 0; k < kV; ++k) r.x[k] = v[k];
+        store8_edge<E, Acc>(row, lo, cols, r);
     }
 }
 
@@ -257,7 +282,7 @@ __host__ __device__ inline TileGeom tile_geom(int MA, int MB, int n_a, int nwarp
 
 // Source row segment for block A: 8 buffer columns starting at i0 of buffer
 // row s, into v (buffer order).
-template <typename Acc, typename SrcE>
+template <bool ADJ, typename Acc, typename SrcE>
 __device__ __forceinline__ void load_source(const PassDesc &d, int M, int S, int a, int s,
                                             int A_off, int i0, Acc (&v)[kV]) {
     const int sg = d.sigma;
@@ -267,7 +292,7 @@ __device__ __forceinline__ void load_source(const PassDesc &d, int M, int S, int
     if (d.lo_image) {
         int row = S * (1 << M) + s;
         const int col = lo - (sg > 0 ? 1 : 0);
-        if (d.cyclic) {
+        if constexpr (ADJ) {
             // gradient rows through the layout's row map
             if (row < d.src_t_first || row > d.src_t_last) {
 #pragma unroll
@@ -286,7 +311,7 @@ __device__ __forceinline__ void load_source(const PassDesc &d, int M, int S, int
         }
     } else {
         const int row = ((S * (1 << M) + s) << d.k0) + a;
-        if (d.cyclic) load8_cyclic<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, lo, d.W, v);
+        if constexpr (ADJ) load8_cyclic<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, lo, d.W, v);
         else load8<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, lo, d.lo.cols, v);
     }
     if (sg < 0) reverse8(v);
@@ -351,6 +376,30 @@ __device__ __forceinline__ DestCols dest_cols(const PassDesc &d, int D, int i0) 
     return c;
 }
 
+// Final-level store of 8 ascending columns p = lo.. of slope t when they do not
+// land as one aligned run: cyclic wrap of X, fhtshift rotation, tile borders.
+template <typename Acc, typename DstE>
+__device__ __noinline__ void store_final_edge(const PassDesc &d, DstE *row, int t, int lo,
+                                              Vec8<Acc> v) {
+    const int W = d.W, sg = d.sigma;
+    int off = sg > 0 ? -d.n : 0;
+    if (d.shift_on) {
+        const int s = fhtshift_amount(t, W, d.shift_win, sg);
+        off += d.shift_inverse ? -s : s;
+    }
+    off %= W;
+    if (off < 0) off += W;
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        const int p = lo + k;
+        if (p >= 0 && p < W) {
+            int X = p + off;
+            if (X >= W) X -= W;
+            row[X] = (DstE)v.x[k];
+        }
+    }
+}
+
 // Store 8 buffer columns of level-k1 row hi_r (values in buffer order).
 template <typename Acc, typename DstE>
 __device__ __forceinline__ void store_dest(const PassDesc &d, const DestCols &c, int hi_r,
@@ -373,30 +422,10 @@ __device__ __forceinline__ void store_dest(const PassDesc &d, const DestCols &c,
         store8<DstE, Acc>(row, c.X0, c.X0 + kV, asc);
         return;
     }
-    const int W = d.W;
-    int off = sg > 0 ? -d.n : 0;
-    if (d.shift_on) {
-        const int s = fhtshift_amount(t, W, d.shift_win, sg);
-        off += d.shift_inverse ? -s : s;
-    }
-    while (off < 0) off += W;
-    while (off >= W) off -= W;
-    const int lo = c.lo;
-    int X0 = lo + off;
-    if (X0 >= W) X0 -= W;
-    if (lo >= 0 && lo + kV <= W && X0 >= 0 && X0 + kV <= W) {
-        store8<DstE, Acc>(row, X0, W, asc);
-    } else {
+    Vec8<Acc> r;
 #pragma unroll
-        for (int k = 0; k < kV; ++k) {
-            const int p = lo + k;
-            if (p >= 0 && p < W) {
-                int X = p + off;
-                if (X >= W) X -= W;
-                row[X] = (DstE)asc[k];
-            }
-        }
-    }
+    for (int k = 0; k < kV; ++k) r.x[k] = asc[k];
+    store_final_edge<Acc, DstE>(d, row, t, c.lo, r);
 }
 
 // Final level of an adjoint: R consecutive output rows y0.. (image rows of the
@@ -503,7 +532,10 @@ __device__ __forceinline__ bool tile_all_black(const PassDesc &d, int M, int a, 
     return lo >= d.black_wc + t_max;
 }
 
-template <int MA, int MB, typename Acc, typename SrcE, typename MidE, typename DstE>
+// ADJ selects the adjoint form at compile time (cyclic columns, row-mapped
+// gradient source, image-gradient destination) so the forward kernels carry
+// none of its code.
+template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
 __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm) {
     constexpr int M = MA + MB, RA = 1 << MA, RB = 1 << MB;
     constexpr int PAD = TilePad<MidE>::kPad;
@@ -516,7 +548,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
     const int sg = d.sigma;
     const int A_off = sg > 0 ? p0 - (1 << (d.k0 + M)) + (1 << d.k0) : p0 + T - 1;
     const int D = sg > 0 ? p0 : p0 + T - 1;
-    const bool black = tile_all_black(d, M, a, p0, T);
+    const bool black = !ADJ && tile_all_black(d, M, a, p0, T);
 
     if constexpr (MB == 0) {
         // single register block: source -> registers -> destination
@@ -524,12 +556,12 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             const int i0 = item * kWarpValid + lane * kV;
             Acc v[RA][kV];
             if (!black) {
-                if (d.lo_image && d.transpose) {
+                if (!ADJ && d.lo_image && d.transpose) {
                     load_source_transposed<RA, Acc, SrcE>(d, M, S, 0, A_off, i0, v);
                 } else {
 #pragma unroll
                     for (int r = 0; r < RA; ++r)
-                        load_source<Acc, SrcE>(d, M, S, a, r, A_off, i0, v[r]);
+                        load_source<ADJ, Acc, SrcE>(d, M, S, a, r, A_off, i0, v[r]);
                 }
                 reg_butterfly<MA, Acc>(v);
             } else {
@@ -540,7 +572,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             }
             if (lane < kLanesValid && i0 < T) {
                 const DestCols dc = dest_cols<Acc, DstE>(d, D, i0);
-                if (d.dst_image) {
+                if (ADJ && d.hi_final) {
                     store_image_block<RA, Acc, DstE>(d, hi_row(d, M, S, a, 0), dc.lo, v);
                 } else {
 #pragma unroll
@@ -558,12 +590,12 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                 const int g = item % RB, wc = item / RB;
                 const int i0 = wc * kWarpValid + lane * kV;
                 Acc v[RA][kV];
-                if (d.lo_image && d.transpose) {
+                if (!ADJ && d.lo_image && d.transpose) {
                     load_source_transposed<RA, Acc, SrcE>(d, M, S, g * RA, A_off, i0, v);
                 } else {
 #pragma unroll
                     for (int r = 0; r < RA; ++r)
-                        load_source<Acc, SrcE>(d, M, S, a, g * RA + r, A_off, i0, v[r]);
+                        load_source<ADJ, Acc, SrcE>(d, M, S, a, g * RA + r, A_off, i0, v[r]);
                 }
                 reg_butterfly<MA, Acc>(v);
                 if (lane < kLanesValid) {
@@ -613,7 +645,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             }
             if (lane < kLanesValid && i0 < T) {
                 const DestCols dc = dest_cols<Acc, DstE>(d, D, i0);
-                if (d.dst_image) {
+                if (ADJ && d.hi_final) {
                     store_image_block<RB, Acc, DstE>(d, hi_row(d, M, S, a, a2 * RB), dc.lo, v);
                 } else {
 #pragma unroll

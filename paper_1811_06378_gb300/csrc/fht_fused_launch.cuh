@@ -11,14 +11,14 @@ namespace fht {
 
 constexpr int kFusedWarps = 8;
 
-template <int MA, int MB, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
 __global__ void __launch_bounds__(kFusedWarps * 32) fused_forward_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_forward_item<MA, MB, Acc, SrcE, MidE, DstE>(d, blockIdx.y, blockIdx.x,
+    fused_forward_item<MA, MB, ADJ, Acc, SrcE, MidE, DstE>(d, blockIdx.y, blockIdx.x,
                                                       reinterpret_cast<MidE *>(smem_raw));
 }
 
-template <int MA, int MB, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
 cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     TileGeom G = tile_geom(MA, MB, d.n_a, kFusedWarps, TilePad<MidE>::kPad);
     d.tile_w = G.tile_out;
@@ -26,31 +26,31 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     dim3 grid(d.tiles, d.s_count * d.a_count);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     size_t smem = MB == 0 ? 0 : (size_t)(1 << (MA + MB)) * G.pitch * sizeof(MidE);
-    auto k = fused_forward_kernel<MA, MB, Acc, SrcE, MidE, DstE>;
+    auto k = fused_forward_kernel<MA, MB, ADJ, Acc, SrcE, MidE, DstE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
     char name[64];
-    snprintf(name, sizeof name, "forward_fused_m%d_%s%s", MA + MB, acc_name<Acc>(),
-             d.hi_final ? "_final" : "");
+    snprintf(name, sizeof name, "%s_m%d_%s%s", ADJ ? "adjoint_fused" : "forward_fused",
+             MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "");
     LaunchScope scope(name, st);
     k<<<grid, kFusedWarps * 32, smem, st>>>(d);
     scope.done();
     return cudaGetLastError();
 }
 
-template <typename Acc, typename SrcE, typename MidE, typename DstE>
+template <bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
 cudaError_t launch_fused_m(int M, const PassDesc &d, cudaStream_t st) {
     switch (M) {
-    case 0: return launch_fused_t<0, 0, Acc, SrcE, MidE, DstE>(d, st);
-    case 1: return launch_fused_t<1, 0, Acc, SrcE, MidE, DstE>(d, st);
-    case 2: return launch_fused_t<2, 0, Acc, SrcE, MidE, DstE>(d, st);
-    case 3: return launch_fused_t<3, 0, Acc, SrcE, MidE, DstE>(d, st);
-    case 4: return launch_fused_t<3, 1, Acc, SrcE, MidE, DstE>(d, st);
-    case 5: return launch_fused_t<3, 2, Acc, SrcE, MidE, DstE>(d, st);
-    default: return launch_fused_t<3, 3, Acc, SrcE, MidE, DstE>(d, st);
+    case 0: return launch_fused_t<0, 0, ADJ, Acc, SrcE, MidE, DstE>(d, st);
+    case 1: return launch_fused_t<1, 0, ADJ, Acc, SrcE, MidE, DstE>(d, st);
+    case 2: return launch_fused_t<2, 0, ADJ, Acc, SrcE, MidE, DstE>(d, st);
+    case 3: return launch_fused_t<3, 0, ADJ, Acc, SrcE, MidE, DstE>(d, st);
+    case 4: return launch_fused_t<3, 1, ADJ, Acc, SrcE, MidE, DstE>(d, st);
+    case 5: return launch_fused_t<3, 2, ADJ, Acc, SrcE, MidE, DstE>(d, st);
+    default: return launch_fused_t<3, 3, ADJ, Acc, SrcE, MidE, DstE>(d, st);
     }
 }
 

@@ -4,6 +4,6 @@
 
 namespace fht {
 cudaError_t launch_fused_f32_f32(int M, const PassDesc &d, cudaStream_t st) {
-    return launch_fused_m<float, float, float, float>(M, d, st);
+    return launch_fused_m<false, float, float, float, float>(M, d, st);
 }
 }  // namespace fht

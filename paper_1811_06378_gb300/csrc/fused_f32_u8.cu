@@ -4,6 +4,6 @@
 
 namespace fht {
 cudaError_t launch_fused_f32_u8(int M, const PassDesc &d, cudaStream_t st) {
-    return launch_fused_m<float, uint8_t, float, float>(M, d, st);
+    return launch_fused_m<false, float, uint8_t, float, float>(M, d, st);
 }
 }  // namespace fht

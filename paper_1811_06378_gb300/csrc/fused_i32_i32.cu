@@ -4,6 +4,6 @@
 
 namespace fht {
 cudaError_t launch_fused_i32_i32(int M, const PassDesc &d, cudaStream_t st) {
-    return launch_fused_m<int32_t, int32_t, int32_t, int32_t>(M, d, st);
+    return launch_fused_m<false, int32_t, int32_t, int32_t, int32_t>(M, d, st);
 }
 }  // namespace fht

@@ -4,6 +4,6 @@
 
 namespace fht {
 cudaError_t launch_fused_i32_u8_u16(int M, const PassDesc &d, cudaStream_t st) {
-    return launch_fused_m<int32_t, uint8_t, uint16_t, uint16_t>(M, d, st);
+    return launch_fused_m<false, int32_t, uint8_t, uint16_t, uint16_t>(M, d, st);
 }
 }  // namespace fht
