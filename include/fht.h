@@ -204,6 +204,8 @@ typedef struct {
     char name[64];
     int launches;
     double total_ms;
+    double alg_bytes;   /* summed algorithmic bytes of those launches: the level
+                           each reads as stored plus the level it writes */
 } fht_kernel_time;
 
 /* Start (or restart) recording; previous records are dropped. */
@@ -211,7 +213,8 @@ fht_status fht_profile_begin(void);
 
 /* Stop recording, synchronize the recorded events and write up to `capacity`
  * per-kernel totals (HOST array) to `out`; *count receives the number of
- * distinct kernel names seen (may exceed capacity). */
+ * distinct kernel names seen (may exceed capacity). Profiling is process-wide
+ * and not meant for use during stream capture. */
 fht_status fht_profile_end(fht_kernel_time *out, int capacity, int *count);
 
 /* Number of kernel launches this library has issued since it was loaded. */

@@ -258,7 +258,7 @@ def adjoint(grad: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: in
 
 class _KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 64), ("launches", ctypes.c_int),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("alg_bytes", ctypes.c_double)]
 
 
 def profile_begin() -> None:
@@ -266,14 +266,15 @@ def profile_begin() -> None:
     _check(lib.fht_profile_begin(), "fht_profile_begin")
 
 
-def profile_end() -> dict[str, tuple[int, float]]:
-    """Stop recording; {kernel name: (launches, summed device ms)}."""
+def profile_end() -> dict[str, tuple[int, float, float]]:
+    """Stop recording; {kernel name: (launches, summed device ms, summed
+    algorithmic bytes)}."""
     cap = 64
     arr = (_KernelTime * cap)()
     cnt = ctypes.c_int()
     _check(lib.fht_profile_end(ctypes.cast(arr, ctypes.c_void_p), cap, ctypes.byref(cnt)),
            "fht_profile_end")
-    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms)
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].alg_bytes)
             for i in range(min(cnt.value, cap))}
 
 

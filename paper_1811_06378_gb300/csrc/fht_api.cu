@@ -28,6 +28,7 @@ bool g_prof_on = false;
 struct ProfRec {
     std::string name;
     cudaEvent_t a, b;
+    double bytes;
 };
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
@@ -47,7 +48,8 @@ cudaEvent_t take_event() {
 
 namespace fht {
 
-LaunchScope::LaunchScope(const char *name, cudaStream_t st) : st_(st) {
+LaunchScope::LaunchScope(const char *name, cudaStream_t st, double alg_bytes)
+    : st_(st), bytes_(alg_bytes) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     std::lock_guard<std::mutex> lk(g_prof_mu);
     on_ = g_prof_on;
@@ -63,7 +65,7 @@ void LaunchScope::done() {
     if (!on_) return;
     cudaEventRecord(b_, st_);
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof.push_back(ProfRec{name_, a_, b_});
+    g_prof.push_back(ProfRec{name_, a_, b_, bytes_});
     on_ = false;
 }
 
@@ -567,7 +569,8 @@ fht_status fhtshift(const void *in, void *out, fht_dtype dtype, int h, int w,
     if (in_pitch < m.W || out_pitch < m.W) return FHT_EINVAL;
     dim3 grid(rows);
     cudaStream_t st = (cudaStream_t)stream;
-    LaunchScope scope(dtype == FHT_I32 ? "fhtshift_i32" : "fhtshift_f32", st);
+    LaunchScope scope(dtype == FHT_I32 ? "fhtshift_i32" : "fhtshift_f32", st,
+                      2.0 * rows * m.W * 4.0);
     if (dtype == FHT_I32)
         fhtshift_kernel<int32_t><<<grid, kBlock, 0, st>>>((const int32_t *)in, (int32_t *)out,
                                                           in_pitch, out_pitch, m, inverse);
@@ -640,7 +643,11 @@ fht_status fht_profile_end(fht_kernel_time *out, int capacity, int *count) {
         g_prof_on = false;
         recs.swap(g_prof);
     }
-    std::map<std::string, std::pair<int, double>> tot;
+    struct Tot {
+        int launches = 0;
+        double ms = 0, bytes = 0;
+    };
+    std::map<std::string, Tot> tot;
     fht_status st = FHT_OK;
     for (auto &r : recs) {
         float ms = 0.f;
@@ -651,8 +658,9 @@ fht_status fht_profile_end(fht_kernel_time *out, int capacity, int *count) {
             st = FHT_ECUDA;
         }
         auto &t = tot[r.name];
-        t.first += 1;
-        t.second += ms;
+        t.launches += 1;
+        t.ms += ms;
+        t.bytes += r.bytes;
     }
     {
         std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -665,8 +673,9 @@ fht_status fht_profile_end(fht_kernel_time *out, int capacity, int *count) {
     for (auto &kv : tot) {
         if (out && i < capacity) {
             snprintf(out[i].name, sizeof out[i].name, "%s", kv.first.c_str());
-            out[i].launches = kv.second.first;
-            out[i].total_ms = kv.second.second;
+            out[i].launches = kv.second.launches;
+            out[i].total_ms = kv.second.ms;
+            out[i].alg_bytes = kv.second.bytes;
         }
         ++i;
     }

@@ -11,11 +11,42 @@ namespace fht {
 
 constexpr int kFusedWarps = 8;
 
-template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
+// Bytes a pass must read and write at least: its source level as stored
+// (image, or compact intermediate rows of the launched groups) and its
+// destination (intermediate rows, output slopes, or image gradient).
+inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t dst_bytes) {
+    const double rows = (double)d.s_count * d.a_count * (1 << M);
+    double rd, wr;
+    if (d.lo_image) {
+        rd = d.cyclic ? (double)(d.src_t_last - d.src_t_first + 1) * d.W * src_bytes
+                      : (double)d.lo.rows * d.lo.cols * src_bytes;
+    } else {
+        rd = rows * d.lo.cols * src_bytes;
+    }
+    if (!d.hi_final) {
+        wr = rows * d.hi.cols * dst_bytes;
+    } else if (d.dst_image) {
+        wr = (double)d.dst_h * d.dst_w * dst_bytes * (d.accumulate ? 2 : 1);
+    } else {
+        const int t0 = d.a_lo << M, t1 = ((d.a_lo + d.a_count) << M) - 1;
+        const int lo = t0 > d.t_first ? t0 : d.t_first, hi = t1 < d.t_last ? t1 : d.t_last;
+        wr = hi >= lo ? (double)(hi - lo + 1) * d.W * dst_bytes : 0.0;
+    }
+    return rd + wr;
+}
+
+template <int MA, int MB, typename Acc, typename SrcE, typename MidE, typename DstE>
 __global__ void __launch_bounds__(kFusedWarps * 32) fused_forward_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_forward_item<MA, MB, ADJ, Acc, SrcE, MidE, DstE>(d, blockIdx.y, blockIdx.x,
-                                                      reinterpret_cast<MidE *>(smem_raw));
+    fused_forward_item<MA, MB, false, Acc, SrcE, MidE, DstE>(
+        d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
+}
+
+template <int MA, int MB, typename Acc, typename SrcE, typename MidE, typename DstE>
+__global__ void __launch_bounds__(kFusedWarps * 32) fused_adjoint_kernel(PassDesc d) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fused_forward_item<MA, MB, true, Acc, SrcE, MidE, DstE>(
+        d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
 }
 
 template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
@@ -26,7 +57,9 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     dim3 grid(d.tiles, d.s_count * d.a_count);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     size_t smem = MB == 0 ? 0 : (size_t)(1 << (MA + MB)) * G.pitch * sizeof(MidE);
-    auto k = fused_forward_kernel<MA, MB, ADJ, Acc, SrcE, MidE, DstE>;
+    void (*k)(PassDesc);
+    if constexpr (ADJ) k = fused_adjoint_kernel<MA, MB, Acc, SrcE, MidE, DstE>;
+    else k = fused_forward_kernel<MA, MB, Acc, SrcE, MidE, DstE>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -35,7 +68,7 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     char name[64];
     snprintf(name, sizeof name, "%s_m%d_%s%s", ADJ ? "adjoint_fused" : "forward_fused",
              MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "");
-    LaunchScope scope(name, st);
+    LaunchScope scope(name, st, pass_alg_bytes(d, MA + MB, sizeof(SrcE), sizeof(DstE)));
     k<<<grid, kFusedWarps * 32, smem, st>>>(d);
     scope.done();
     return cudaGetLastError();

@@ -12,14 +12,16 @@ namespace fht {
 
 // Counts a kernel launch and, while profiling is on (fht_profile_begin),
 // brackets it with CUDA events on its stream: construct right before the
-// launch, call done() right after it.
+// launch, call done() right after it. alg_bytes: the bytes the launch must
+// move at least (the level it reads as stored plus the level it writes).
 class LaunchScope {
   public:
-    LaunchScope(const char *name, cudaStream_t st);
+    LaunchScope(const char *name, cudaStream_t st, double alg_bytes);
     void done();
 
   private:
     cudaStream_t st_;
+    double bytes_;
     bool on_ = false;
     std::string name_;
     cudaEvent_t a_ = nullptr, b_ = nullptr;
