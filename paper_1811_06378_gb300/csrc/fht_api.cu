@@ -270,7 +270,14 @@ PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &fina
     d.shift_inverse = fm.shift_inverse;
     d.shift_win = P.w_in;
     d.black_wc = P.w_c;
-    d.n_a = P.m[p] >= 4 ? (acc_is_u16_mid(P, p) ? g_tune.n_a_u16 : g_tune.n_a_wide) : 1;
+    // block A has 2^MB items per warp-column: widen it until every warp has one
+    if (P.m[p] >= 4) {
+        const int rb = 1 << (P.m[p] - 3);
+        const int base = acc_is_u16_mid(P, p) ? g_tune.n_a_u16 : g_tune.n_a_wide;
+        d.n_a = std::max(base, 8 / rb);
+    } else {
+        d.n_a = 1;
+    }
     return d;
 }
 

@@ -91,59 +91,66 @@ __device__ __noinline__ void store8_edge(E *row, int lo, int cols, Vec8<Acc> v) 
     }
 }
 
-// v[k] = row[lo + k] for k < 8, zero outside [0, cols). Fast path: the aligned
-// granules covering the 8 elements are loaded whole; the start offset inside
-// the first granule selects the elements with selects and byte permutes.
+// v[k] = row[lo + k] for k < 8; all 8 must lie inside the row. The aligned
+// granules covering them are loaded whole; the start offset inside the first
+// granule selects the elements with selects and byte permutes (no branches,
+// so the loads of several rows can all be in flight together).
+template <typename E, typename Acc>
+__device__ __forceinline__ void load8_fast(const E *row, int lo, Acc (&v)[kV]) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(row + lo);
+    if constexpr (sizeof(E) == 1) {
+        const int delta = (int)(a & 7);
+        const uint2 *g = reinterpret_cast<const uint2 *>(a & ~(uintptr_t)7);
+        uint2 q0 = __ldg(g), q1 = make_uint2(0, 0);
+        if (delta) q1 = __ldg(g + 1);
+        const uint32_t w0 = q0.x, w1 = q0.y, w2 = q1.x, w3 = q1.y;
+        const bool hi = delta >= 4;
+        const uint32_t u0 = hi ? w1 : w0, u1 = hi ? w2 : w1, u2 = hi ? w3 : w2;
+        const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)(delta & 3);
+        const uint32_t b0 = __byte_perm(u0, u1, sel), b1 = __byte_perm(u1, u2, sel);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (Acc)(int32_t)((b0 >> (8 * k)) & 0xffu);
+            v[k + 4] = (Acc)(int32_t)((b1 >> (8 * k)) & 0xffu);
+        }
+    } else if constexpr (sizeof(E) == 2) {
+        const int delta = (int)((a & 15) >> 1);
+        const uint4 *g = reinterpret_cast<const uint4 *>(a & ~(uintptr_t)15);
+        uint4 q0 = __ldg(g), q1 = make_uint4(0, 0, 0, 0);
+        if (delta) q1 = __ldg(g + 1);
+        const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        const int j = delta >> 1;
+        uint32_t u[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) u[i] = sel4(w[i], w[i + 1 < 8 ? i + 1 : 7],
+                                              w[i + 2 < 8 ? i + 2 : 7], w[i + 3 < 8 ? i + 3 : 7], j);
+        const uint32_t sel = (delta & 1) ? 0x5432u : 0x3210u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t pr = __byte_perm(u[i], u[i + 1], sel);
+            v[2 * i] = (Acc)(int32_t)(pr & 0xffffu);
+            v[2 * i + 1] = (Acc)(int32_t)(pr >> 16);
+        }
+    } else {
+        const int delta = (int)((a & 15) >> 2);
+        const uint4 *g = reinterpret_cast<const uint4 *>(a & ~(uintptr_t)15);
+        uint4 q0 = __ldg(g), q1 = __ldg(g + 1), q2 = make_uint4(0, 0, 0, 0);
+        if (delta) q2 = __ldg(g + 2);
+        const uint32_t w[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y,
+                                q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+        using IsF = std::integral_constant<bool, std::is_same<Acc, float>::value &&
+                                                     std::is_same<E, float>::value>;
+#pragma unroll
+        for (int k = 0; k < kV; ++k)
+            v[k] = from_word<Acc>(sel4(w[k], w[k + 1], w[k + 2], w[k + 3], delta), IsF());
+    }
+}
+
+// v[k] = row[lo + k] for k < 8, zero outside [0, cols).
 template <typename E, typename Acc>
 __device__ __forceinline__ void load8(const E *row, int lo, int cols, Acc (&v)[kV]) {
     if (lo >= 0 && lo + kV <= cols) {
-        const uintptr_t a = reinterpret_cast<uintptr_t>(row + lo);
-        if constexpr (sizeof(E) == 1) {
-            const int delta = (int)(a & 7);
-            const uint2 *g = reinterpret_cast<const uint2 *>(a & ~(uintptr_t)7);
-            uint2 q0 = __ldg(g), q1 = make_uint2(0, 0);
-            if (delta) q1 = __ldg(g + 1);
-            const uint32_t w0 = q0.x, w1 = q0.y, w2 = q1.x, w3 = q1.y;
-            const bool hi = delta >= 4;
-            const uint32_t u0 = hi ? w1 : w0, u1 = hi ? w2 : w1, u2 = hi ? w3 : w2;
-            const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)(delta & 3);
-            const uint32_t b0 = __byte_perm(u0, u1, sel), b1 = __byte_perm(u1, u2, sel);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v[k] = (Acc)(int32_t)((b0 >> (8 * k)) & 0xffu);
-                v[k + 4] = (Acc)(int32_t)((b1 >> (8 * k)) & 0xffu);
-            }
-        } else if constexpr (sizeof(E) == 2) {
-            const int delta = (int)((a & 15) >> 1);
-            const uint4 *g = reinterpret_cast<const uint4 *>(a & ~(uintptr_t)15);
-            uint4 q0 = __ldg(g), q1 = make_uint4(0, 0, 0, 0);
-            if (delta) q1 = __ldg(g + 1);
-            const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-            const int j = delta >> 1;
-            uint32_t u[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) u[i] = sel4(w[i], w[i + 1 < 8 ? i + 1 : 7],
-                                                  w[i + 2 < 8 ? i + 2 : 7], w[i + 3 < 8 ? i + 3 : 7], j);
-            const uint32_t sel = (delta & 1) ? 0x5432u : 0x3210u;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint32_t pr = __byte_perm(u[i], u[i + 1], sel);
-                v[2 * i] = (Acc)(int32_t)(pr & 0xffffu);
-                v[2 * i + 1] = (Acc)(int32_t)(pr >> 16);
-            }
-        } else {
-            const int delta = (int)((a & 15) >> 2);
-            const uint4 *g = reinterpret_cast<const uint4 *>(a & ~(uintptr_t)15);
-            uint4 q0 = __ldg(g), q1 = __ldg(g + 1), q2 = make_uint4(0, 0, 0, 0);
-            if (delta) q2 = __ldg(g + 2);
-            const uint32_t w[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y,
-                                    q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
-            using IsF = std::integral_constant<bool, std::is_same<Acc, float>::value &&
-                                                         std::is_same<E, float>::value>;
-#pragma unroll
-            for (int k = 0; k < kV; ++k)
-                v[k] = from_word<Acc>(sel4(w[k], w[k + 1], w[k + 2], w[k + 3], delta), IsF());
-        }
+        load8_fast<E, Acc>(row, lo, v);
     } else {
         const Vec8<Acc> r = load8_edge<E, Acc>(row, lo, cols);
 #pragma unroll
@@ -345,6 +352,101 @@ __device__ __forceinline__ void load_source_transposed(const PassDesc &d, int M,
     for (int r = 0; r < RA; ++r)
 #pragma unroll
         for (int k = 0; k < kV; ++k) v[r][k] = sg > 0 ? blk[k][r] : blk[kV - 1 - k][r];
+}
+
+// ------------------------------------------------------------ block A source
+
+template <typename Acc, int R>
+struct Block {
+    Acc x[R][kV];
+};
+
+// Rare edge items (tile borders, image borders, wraps): per-row checked loads,
+// out of line.
+template <int RA, bool ADJ, typename Acc, typename SrcE>
+__device__ __noinline__ Block<Acc, RA> load_block_a_edge(const PassDesc &d, int M, int S, int a,
+                                                         int s0, int A_off, int i0) {
+    Block<Acc, RA> b;
+    if (!ADJ && d.lo_image && d.transpose) {
+        load_source_transposed<RA, Acc, SrcE>(d, M, S, s0, A_off, i0, b.x);
+    } else {
+#pragma unroll
+        for (int r = 0; r < RA; ++r) load_source<ADJ, Acc, SrcE>(d, M, S, a, s0 + r, A_off, i0, b.x[r]);
+    }
+    return b;
+}
+
+// Block A's RA source rows s0.. for this lane's 8 buffer columns i0..i0+7.
+// Whether every row and every lane of the warp item (columns wbase ..
+// wbase + 255) lies inside the source is decided once, warp-uniformly; the
+// common interior case then issues all rows' loads without branches.
+template <int RA, bool ADJ, typename Acc, typename SrcE>
+__device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, int a, int s0,
+                                             int A_off, int wbase, int i0, Acc (&v)[RA][kV]) {
+    const int sg = d.sigma;
+    const int splus = sg > 0 ? 1 : 0;
+    // ascending source-column range [lo_min, hi_max) over the warp item
+    int lo_min, hi_max;
+    if (sg > 0) {
+        lo_min = A_off + wbase + a * s0;
+        hi_max = A_off + wbase + 32 * kV + a * (s0 + RA - 1);
+    } else {
+        lo_min = A_off - wbase - (32 * kV - 1) - a * (s0 + RA - 1);
+        hi_max = A_off - wbase - a * s0 + 1;
+    }
+    const SrcE *base = reinterpret_cast<const SrcE *>(d.lo.ptr);
+    const int row0 = S * (1 << M) + s0;   // first level-0 row (image sources)
+    bool interior;
+    if (d.lo_image) {
+        const int c0 = lo_min - splus, c1 = hi_max - splus;
+        if constexpr (ADJ) {
+            interior = row0 >= d.src_t_first && row0 + RA - 1 <= d.src_t_last && c0 >= 0 &&
+                       c1 <= d.W;
+        } else if (d.transpose) {
+            interior = c0 >= 0 && c1 <= d.lo.cols && row0 + kV <= d.lo.rows;
+        } else {
+            interior = c0 >= 0 && c1 <= d.lo.cols && row0 + RA <= d.lo.rows;
+        }
+    } else {
+        interior = lo_min >= 0 && hi_max <= (ADJ ? d.W : d.lo.cols);
+    }
+    if (!interior) {
+        const Block<Acc, RA> b = load_block_a_edge<RA, ADJ, Acc, SrcE>(d, M, S, a, s0, A_off, i0);
+#pragma unroll
+        for (int r = 0; r < RA; ++r)
+#pragma unroll
+            for (int k = 0; k < kV; ++k) v[r][k] = b.x[r][k];
+        return;
+    }
+    if (!ADJ && d.lo_image && d.transpose) {
+        // 8 image rows (buffer columns) x 8 image columns (rows s0..)
+        const int p_first = A_off + sg * i0;
+        const int lo = (sg > 0 ? p_first : p_first - (kV - 1)) - splus;
+        Acc blk[kV][kV];
+#pragma unroll
+        for (int k = 0; k < kV; ++k)
+            load8_fast<SrcE, Acc>(base + (int64_t)(lo + k) * d.lo.pitch, row0, blk[k]);
+#pragma unroll
+        for (int r = 0; r < RA; ++r)
+#pragma unroll
+            for (int k = 0; k < kV; ++k) v[r][k] = sg > 0 ? blk[k][r] : blk[kV - 1 - k][r];
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+        const int s = s0 + r;
+        const int p_first = A_off + sg * (i0 + a * s);
+        int lo = sg > 0 ? p_first : p_first - (kV - 1);
+        int64_t row;
+        if (d.lo_image) {
+            lo -= splus;
+            row = ADJ ? (int64_t)d.src_row_base + (int64_t)d.src_row_dir * (row0 + r) : row0 + r;
+        } else {
+            row = ((int64_t)(S * (1 << M) + s) << d.k0) + a;
+        }
+        load8_fast<SrcE, Acc>(base + row * d.lo.pitch, lo, v[r]);
+        if (sg < 0) reverse8(v[r]);
+    }
 }
 
 // Destination of one lane's 8 buffer columns (i0..i0+7): everything that does
@@ -556,13 +658,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             const int i0 = item * kWarpValid + lane * kV;
             Acc v[RA][kV];
             if (!black) {
-                if (!ADJ && d.lo_image && d.transpose) {
-                    load_source_transposed<RA, Acc, SrcE>(d, M, S, 0, A_off, i0, v);
-                } else {
-#pragma unroll
-                    for (int r = 0; r < RA; ++r)
-                        load_source<ADJ, Acc, SrcE>(d, M, S, a, r, A_off, i0, v[r]);
-                }
+                load_block_a<RA, ADJ, Acc, SrcE>(d, M, S, a, 0, A_off, item * kWarpValid, i0, v);
                 reg_butterfly<MA, Acc>(v);
             } else {
 #pragma unroll
@@ -590,13 +686,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                 const int g = item % RB, wc = item / RB;
                 const int i0 = wc * kWarpValid + lane * kV;
                 Acc v[RA][kV];
-                if (!ADJ && d.lo_image && d.transpose) {
-                    load_source_transposed<RA, Acc, SrcE>(d, M, S, g * RA, A_off, i0, v);
-                } else {
-#pragma unroll
-                    for (int r = 0; r < RA; ++r)
-                        load_source<ADJ, Acc, SrcE>(d, M, S, a, g * RA + r, A_off, i0, v[r]);
-                }
+                load_block_a<RA, ADJ, Acc, SrcE>(d, M, S, a, g * RA, A_off, wc * kWarpValid, i0, v);
                 reg_butterfly<MA, Acc>(v);
                 if (lane < kLanesValid) {
                     const int pos = (8 + PAD) * (i0 >> 3);   // i0 is a multiple of 8
