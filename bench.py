@@ -17,6 +17,10 @@ write) before every timed step, W >= 3 warm-up steps. Per-row times, the
 plain single-quadrant forward (the headline FHT at 4096^2 int32) and the
 batched path are reported under "rows".
 
+Rows also include the batched path: 512 uint8 edge maps with sides
+log-uniform in [64, 1024] in one persistent launch, against one fht_forward
+call per image.
+
 Multi-GPU: replicas only (each rank transforms its own image, no collective
 on the data path); value sums all ranks, time is the max over ranks.
 
@@ -356,6 +360,26 @@ def run_ours(args):
         rows["range_pm15deg_int32"] = row_entry(
             row_range, S * S + sum(t.numel() for t in rng_out.values()) * 4, S * S)
         rows["adjoint_full_f32"] = row_entry(row_adjoint, R * Wf * 4 + S * S * 4, S * S)
+        # batched: 512 uint8 edge maps, sides log-uniform in [64, 1024], each padded
+        # to its own power of two, Q0 into int32 -- one persistent launch versus
+        # one fht_forward call per image
+        from workloads import batch_shapes, edge_batch
+        shapes = batch_shapes(512, seed=3)
+        bimgs = [torch.from_numpy(a).to(dev) for a in edge_batch(shapes, seed=3)]
+        plan = fht.BatchPlan(shapes, 0)
+        bws = plan.workspace(dev)
+        bouts = [torch.empty(sh, dtype=torch.int32, device=dev) for sh in plan.out_shapes]
+        bpix = sum(h * w for h, w in shapes)
+        balg = bpix + sum(n * W * 4 for n, W in plan.out_shapes)
+        pws = torch.empty(max(fht.workspace_size(1024, 1024, fht.LAYOUT_QUADRANT, 0,
+                                                 torch.uint8, torch.int32), 1),
+                          dtype=torch.uint8, device=dev)
+        rows["batched_512_u8_q0"] = row_entry(lambda: plan.forward(bimgs, bouts, bws), balg, bpix)
+        rows["per_image_512_u8_q0"] = row_entry(
+            lambda: [fht.forward(x, 0, out=o, workspace=pws) for x, o in zip(bimgs, bouts)],
+            balg, bpix)
+        rows["batched_512_u8_q0"]["speedup_vs_per_image"] = (
+            rows["per_image_512_u8_q0"]["ms"] / rows["batched_512_u8_q0"]["ms"])
 
     # ---- roofline of the dominant kernel (largest share of the timed step):
     # the library's CUDA events on the launch stream give its launch times,

@@ -194,6 +194,52 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
                        void *grad_img, int64_t out_pitch, void *workspace,
                        size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------ batched
+ * Many images of different sizes in one persistent launch. Each image is
+ * transformed exactly as fht_forward would transform it (same quadrant and
+ * types for the whole batch), padded to its own power of two; the launch takes
+ * work items of all images from one queue, ordered by pass, and an item of a
+ * later pass waits for its image's previous pass (the waits are bounded; see
+ * fht_batched_status). Not in the paper: batching is how the library runs many
+ * small transforms at once. Supported: uint8 -> int32 and float32 -> float32,
+ * images up to 4096 padded rows (4096 padded columns for Q2/Q3). */
+typedef struct fht_plan fht_plan;   /* opaque, host-side */
+
+typedef struct {
+    const void *img;     /* DEVICE pointer to image j, h_j x w_j, pitch img_pitch */
+    int64_t img_pitch;   /* elements, >= w_j */
+    void *out;           /* DEVICE pointer to its quadrant, n_j x W_j, pitch out_pitch */
+    int64_t out_pitch;   /* elements, >= W_j (fht_query_shape) */
+} fht_image_desc;
+
+/* Plan a batch of `count` images with sizes hs[j] x ws[j] (HOST arrays).
+ * Writes the plan (free with fht_plan_destroy) and the device workspace it
+ * needs (intermediate levels of every image, the work tables and counters).
+ * Allocates only host memory (pinned staging for the tables). */
+fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_quadrant q,
+                                   fht_dtype in_t, fht_dtype acc_t, fht_plan **plan,
+                                   size_t *workspace_bytes);
+
+/* Transform the batch: descs is a HOST array of `count` descriptors, checked
+ * against the plan; workspace is >= workspace_bytes, 256-byte aligned. One
+ * host-to-device copy of the tables, one memset and one kernel launch on
+ * `stream`, all capturable in a CUDA graph (a replay reuses the descriptors
+ * given at capture). A plan serves one stream at a time. */
+fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void *workspace,
+                               size_t workspace_bytes, void *stream);
+
+/* Wait for `stream` and report the last batched launch's device status in
+ * `workspace`: FHT_OK, or FHT_ETIMEOUT if a pass dependency wait exceeded
+ * its budget (the affected items were skipped and the launch still ended). */
+fht_status fht_batched_status(const fht_plan *plan, const void *workspace, void *stream);
+
+/* Test hook: the clock budget (SM cycles) of each dependency wait, and a
+ * number added to every dependency target (dep_bias > 0 makes the waits
+ * unsatisfiable, so that tests can check the timeout path). */
+fht_status fht_batched_test_hooks(fht_plan *plan, long long wait_budget_cycles, int dep_bias);
+
+void fht_plan_destroy(fht_plan *plan);
+
 /* ------------------------------------------------------------ profiling
  * Kernel-level timing for benchmarks; normal use never needs it. Not in the
  * paper. While profiling is on, every kernel launch made by this library is

@@ -23,7 +23,7 @@ __all__ = [
     "Q0", "Q1", "Q2", "Q3", "LAYOUT_QUADRANT", "LAYOUT_FULL", "FHTError", "lib",
     "query_shape", "full_shape", "full_row_to_quadrant", "angle_to_slopes",
     "workspace_size", "forward", "forward_range", "full_quadrants", "fhtshift",
-    "adjoint", "FHTFunction", "profile_begin", "profile_end", "launch_count",
+    "adjoint", "FHTFunction", "profile_begin", "profile_end", "launch_count", "BatchPlan",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -61,6 +61,12 @@ def _load() -> ctypes.CDLL:
         "fht_full_quadrants": (i, [vp, i, i, i, i64, vp, i, i64, i, vp, sz, vp]),
         "fhtshift": (i, [vp, vp, i, i, i, i, i, i, i64, i64, vp]),
         "fht_adjoint": (i, [vp, i, i, i, i, i, i64, vp, i64, vp, sz, vp]),
+        "fht_plan_create_batched": (i, [ctypes.POINTER(i), ctypes.POINTER(i), i, i, i, i,
+                                        ctypes.POINTER(vp), ctypes.POINTER(sz)]),
+        "fht_forward_batched": (i, [vp, vp, vp, sz, vp]),
+        "fht_batched_status": (i, [vp, vp, vp]),
+        "fht_batched_test_hooks": (i, [vp, ctypes.c_longlong, i]),
+        "fht_plan_destroy": (None, [vp]),
         "fht_profile_begin": (i, []),
         "fht_profile_end": (i, [vp, i, ip]),
         "fht_launch_count": (ctypes.c_longlong, []),
@@ -252,6 +258,79 @@ def adjoint(grad: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: in
     _check(lib.fht_adjoint(_ptr(grad), t, h, w, layout, q, ip, _ptr(out), op, _ptr(ws),
                            _nbytes(ws), _stream(stream)), "fht_adjoint")
     return out
+
+
+# ------------------------------------------------------------------ batched
+
+class _ImageDesc(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("img_pitch", ctypes.c_int64),
+                ("out", ctypes.c_void_p), ("out_pitch", ctypes.c_int64)]
+
+
+class BatchPlan:
+    """Many images of different sizes, each transformed as `forward` would
+    (one quadrant, one type pair), in one persistent launch."""
+
+    def __init__(self, shapes, q: int = Q0, in_dtype: torch.dtype = torch.uint8,
+                 acc: torch.dtype = torch.int32):
+        self.shapes = [(int(h), int(w)) for h, w in shapes]
+        self.q, self.in_dtype, self.acc = q, in_dtype, acc
+        n = len(self.shapes)
+        hs = (ctypes.c_int * n)(*[h for h, _ in self.shapes])
+        ws = (ctypes.c_int * n)(*[w for _, w in self.shapes])
+        plan = ctypes.c_void_p()
+        nbytes = ctypes.c_size_t()
+        _check(lib.fht_plan_create_batched(hs, ws, n, q, _DTYPE[in_dtype], _DTYPE[acc],
+                                           ctypes.byref(plan), ctypes.byref(nbytes)),
+               "fht_plan_create_batched")
+        self._plan = plan
+        self.workspace_bytes = nbytes.value
+        self.out_shapes = [query_shape(h, w, q) for h, w in self.shapes]
+
+    def workspace(self, device) -> torch.Tensor:
+        return torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=device)
+
+    def forward(self, imgs, outs=None, workspace: torch.Tensor | None = None,
+                stream=None):
+        if len(imgs) != len(self.shapes):
+            raise ValueError("one image per planned shape")
+        dev = imgs[0].device
+        if outs is None:
+            outs = [torch.empty(sh, dtype=self.acc, device=dev) for sh in self.out_shapes]
+        descs = (_ImageDesc * len(imgs))()
+        for j, (x, o) in enumerate(zip(imgs, outs)):
+            it, ip = _dev2d(x, "img")
+            ot, op = _dev2d(o, "out")
+            if tuple(x.shape) != self.shapes[j] or x.dtype != self.in_dtype:
+                raise ValueError(f"image {j}: expected {self.shapes[j]} {self.in_dtype}")
+            _shape(o, self.out_shapes[j], f"out[{j}]")
+            if o.dtype != self.acc:
+                raise ValueError(f"out[{j}] must be {self.acc}")
+            descs[j] = _ImageDesc(x.data_ptr(), ip, o.data_ptr(), op)
+        ws = self.workspace(dev) if workspace is None else workspace
+        if ws.numel() * ws.element_size() < self.workspace_bytes:
+            raise ValueError("workspace too small")
+        _check(lib.fht_forward_batched(self._plan, ctypes.cast(descs, ctypes.c_void_p),
+                                       _ptr(ws), _nbytes(ws), _stream(stream)),
+               "fht_forward_batched")
+        self._last_ws = ws
+        return outs
+
+    def status(self, workspace: torch.Tensor | None = None, stream=None) -> int:
+        """Device status of the last launch on `workspace` (0 = ok, 5 = a
+        dependency wait timed out); waits for the stream."""
+        ws = self._last_ws if workspace is None else workspace
+        return int(lib.fht_batched_status(self._plan, _ptr(ws), _stream(stream)))
+
+    def set_test_hooks(self, wait_budget_cycles: int, dep_bias: int) -> None:
+        _check(lib.fht_batched_test_hooks(self._plan, wait_budget_cycles, dep_bias),
+               "fht_batched_test_hooks")
+
+    def __del__(self):
+        plan = getattr(self, "_plan", None)
+        if plan is not None and plan.value:
+            lib.fht_plan_destroy(plan)
+            self._plan = None
 
 
 # ------------------------------------------------------------------ profiling

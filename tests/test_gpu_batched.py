@@ -1,0 +1,88 @@
+"""The batched persistent launch against per-image transforms (bit-exact),
+under CUDA-graph capture and replay, and its bounded dependency waits."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from workloads import batch_shapes, edge_batch, random_image
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fht():
+    import paper_1811_06378_gb300 as m
+    return m
+
+
+def _mixed_shapes():
+    # single-pass (n <= 64) and two-pass images, ragged sizes, a 1 x 1 image
+    return [(1, 1), (3, 70), (64, 64), (65, 33), (100, 300), (257, 129), (512, 1000),
+            (1000, 77), (33, 1024), (1024, 1024)]
+
+
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
+def test_batched_u8_matches_per_image(fht, q):
+    shapes = _mixed_shapes()
+    imgs = [torch.from_numpy(a).cuda() for a in edge_batch(shapes, seed=q)]
+    plan = fht.BatchPlan(shapes, q)
+    outs = plan.forward(imgs)
+    assert plan.status() == 0
+    for x, o in zip(imgs, outs):
+        assert torch.equal(o, fht.forward(x, q))
+    # spot-check against the oracle
+    for j in (0, 3, 5):
+        assert (outs[j].cpu().numpy() == O.quadrant(imgs[j].cpu().numpy(), q)).all()
+
+
+def test_batched_f32_matches_per_image(fht):
+    shapes = [(50, 60), (128, 128), (300, 200)]
+    imgs = [torch.from_numpy(random_image(h, w, "f32", seed=h)).cuda() for h, w in shapes]
+    plan = fht.BatchPlan(shapes, 0, torch.float32, torch.float32)
+    outs = plan.forward(imgs)
+    for x, o in zip(imgs, outs):
+        assert torch.equal(o, fht.forward(x, 0, acc=torch.float32))
+
+
+def test_batched_512_images_graph_replay(fht):
+    """The 512-image batch (sides log-uniform in [64, 1024], 8% edges) in one
+    launch captured in a CUDA graph; replays are idempotent and equal the
+    per-image transforms."""
+    shapes = batch_shapes(512, seed=3)
+    imgs = [torch.from_numpy(a).cuda() for a in edge_batch(shapes, seed=3)]
+    plan = fht.BatchPlan(shapes, 0)
+    ws = plan.workspace("cuda")
+    outs = [torch.zeros(sh, dtype=torch.int32, device="cuda") for sh in plan.out_shapes]
+    plan.forward(imgs, outs, ws)          # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.forward(imgs, outs, ws, stream=s)
+    for o in outs:
+        o.fill_(-1)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert plan.status(ws) == 0
+    for j, (x, o) in enumerate(zip(imgs, outs)):
+        assert torch.equal(o, fht.forward(x, 0)), j
+
+
+def test_batched_wait_timeout_is_reported(fht):
+    """An unsatisfiable dependency (test hook) makes the bounded waits run
+    out: the launch ends, reports FHT_ETIMEOUT, and the context stays usable."""
+    shapes = [(256, 256), (300, 100)]     # two passes each: second passes wait
+    imgs = [torch.from_numpy(a).cuda() for a in edge_batch(shapes, seed=9)]
+    plan = fht.BatchPlan(shapes, 0)
+    plan.set_test_hooks(wait_budget_cycles=2_000_000, dep_bias=1)   # ~1 ms per wait
+    plan.forward(imgs)
+    assert plan.status() == 5
+    plan.set_test_hooks(wait_budget_cycles=4_000_000_000, dep_bias=0)
+    outs = plan.forward(imgs)
+    assert plan.status() == 0
+    for x, o in zip(imgs, outs):
+        assert torch.equal(o, fht.forward(x, 0))
