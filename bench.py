@@ -380,6 +380,26 @@ def run_ours(args):
             balg, bpix)
         rows["batched_512_u8_q0"]["speedup_vs_per_image"] = (
             rows["per_image_512_u8_q0"]["ms"] / rows["batched_512_u8_q0"]["ms"])
+        del bimgs, bouts, bws, plan
+        # differentiable path: one gradient-descent step of the 64 x 1024^2 FP32
+        # reconstruction (full-image forward + adjoint per image, plus the update)
+        from workloads import ellipse_phantom
+        B5, n5 = 64, 1024
+        xt = torch.from_numpy(np.stack([ellipse_phantom(n5, seed=100 + i)
+                                        for i in range(B5)])).to(dev)
+        b5 = fht.FHTFunction.apply(xt)
+        x5 = torch.zeros_like(xt)
+        R5, W5 = fht.full_shape(n5, n5)
+
+        def gd_step():
+            with torch.no_grad():
+                r = fht.FHTFunction.apply(x5) - b5
+                g = torch.stack([fht.adjoint(ri, n5, n5) for ri in r])
+                x5.sub_(1e-6 * g)
+
+        rows["gd_step_64x1024_f32"] = row_entry(
+            gd_step, B5 * (2 * n5 * n5 * 4 + 2 * R5 * W5 * 4), B5 * n5 * n5)
+        del xt, b5, x5
 
     # ---- roofline of the dominant kernel (largest share of the timed step):
     # the library's CUDA events on the launch stream give its launch times,

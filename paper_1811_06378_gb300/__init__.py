@@ -366,18 +366,27 @@ class FHTFunction(torch.autograd.Function):
     """Differentiable FP32 Hough transform: forward by the CUDA butterfly,
     backward by the hand-written adjoint kernels (its exact transpose).
 
-    apply(x, layout=LAYOUT_FULL, q=Q0) for a 2-D float32 CUDA tensor x."""
+    apply(x, layout=LAYOUT_FULL, q=Q0) for a float32 CUDA tensor x of shape
+    (h, w), or (B, h, w) for a batch (one library call per image)."""
 
     @staticmethod
     def forward(ctx, x: torch.Tensor, layout: int = LAYOUT_FULL, q: int = Q0):
-        ctx.h, ctx.w = x.shape
+        ctx.h, ctx.w = x.shape[-2:]
         ctx.layout, ctx.q = layout, q
         x = x.contiguous()
-        if layout == LAYOUT_FULL:
-            return full_quadrants(x, acc=torch.float32)
-        return forward(x, q, acc=torch.float32)
+
+        def one(img):
+            if layout == LAYOUT_FULL:
+                return full_quadrants(img, acc=torch.float32)
+            return forward(img, q, acc=torch.float32)
+
+        if x.dim() == 2:
+            return one(x)
+        return torch.stack([one(img) for img in x])
 
     @staticmethod
     def backward(ctx, g: torch.Tensor):
-        gx = adjoint(g.contiguous(), ctx.h, ctx.w, ctx.layout, ctx.q)
-        return gx, None, None
+        g = g.contiguous()
+        if g.dim() == 2:
+            return adjoint(g, ctx.h, ctx.w, ctx.layout, ctx.q), None, None
+        return torch.stack([adjoint(gi, ctx.h, ctx.w, ctx.layout, ctx.q) for gi in g]), None, None
