@@ -164,6 +164,24 @@ def traffic_per_launch(kernel: str, side: int):
     return None if k is None else float(k["dram_bytes_per_launch"])
 
 
+def reduce_max_ms(total_ms: float, world: int, device) -> float:
+    """The slowest rank's timed total (replicas run concurrently; the job takes
+    as long as its slowest rank)."""
+    if world <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix_s(world: int, pixels_per_rank_step: int, ms_per_step: float) -> float:
+    """Input megapixels per second summed over all ranks (weak scaling: every
+    rank transforms its own image each step)."""
+    return world * pixels_per_rank_step / 1e6 / (ms_per_step / 1e3)
+
+
 def dist_setup():
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -334,13 +352,9 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop() if clocks else None
 
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_ms(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * S * S / 1e6 / (ms_per_step / 1e3)
+    value = whole_job_mpix_s(world, S * S, ms_per_step)
 
     # ---- per-row measurements (same flush discipline)
     peak, peak_kind = load_peaks()
