@@ -56,27 +56,28 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     return v;
 }
 
-template <int MA, int MB, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int MA, int MB, int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
 __device__ __forceinline__ void run_item(const PassDesc &d, int gy, int tile, unsigned char *sm) {
-    fused_forward_item<MA, MB, false, Acc, SrcE, MidE, DstE>(d, gy, tile,
-                                                             reinterpret_cast<MidE *>(sm));
+    fused_forward_item<MA, MB, SG, false, Acc, SrcE, MidE, DstE>(d, gy, tile,
+                                                                 reinterpret_cast<MidE *>(sm));
 }
 
-template <typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
 __device__ __forceinline__ void run_item_m(int m, const PassDesc &d, int gy, int tile,
                                            unsigned char *sm) {
     switch (m) {
-    case 0: run_item<0, 0, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 1: run_item<1, 0, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 2: run_item<2, 0, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 3: run_item<3, 0, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 4: run_item<3, 1, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 5: run_item<3, 2, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    default: run_item<3, 3, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 0: run_item<0, 0, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 1: run_item<1, 0, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 2: run_item<2, 0, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 3: run_item<3, 0, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 4: run_item<3, 1, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 5: run_item<3, 2, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    default: run_item<3, 3, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
     }
 }
 
-template <bool F32>
+// one batch = one quadrant, so one sign: the kernel is instantiated per sign
+template <bool F32, int SG>
 __global__ void __launch_bounds__(kWarps * 32, 2)
     batched_forward_kernel(const BatchSeg *segs, int n_segs, int total_items,
                            const fht_image_desc *descs, unsigned char *ws, Counters *ctr,
@@ -143,17 +144,17 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
             const int local = item - sg.item_begin;
             const int gy = local / sg.tiles, tile = local - gy * sg.tiles;
             if constexpr (F32) {
-                run_item_m<float, float, float, float>(sg.m, d, gy, tile, smem_raw);
+                run_item_m<SG, float, float, float, float>(sg.m, d, gy, tile, smem_raw);
             } else {
                 switch (sg.variant) {
                 case kVarU8Final:
-                    run_item_m<int32_t, uint8_t, uint16_t, int32_t>(sg.m, d, gy, tile, smem_raw);
+                    run_item_m<SG, int32_t, uint8_t, uint16_t, int32_t>(sg.m, d, gy, tile, smem_raw);
                     break;
                 case kVarU8Level:
-                    run_item_m<int32_t, uint8_t, uint16_t, uint16_t>(sg.m, d, gy, tile, smem_raw);
+                    run_item_m<SG, int32_t, uint8_t, uint16_t, uint16_t>(sg.m, d, gy, tile, smem_raw);
                     break;
                 default:
-                    run_item_m<int32_t, uint16_t, int32_t, int32_t>(sg.m, d, gy, tile, smem_raw);
+                    run_item_m<SG, int32_t, uint16_t, int32_t, int32_t>(sg.m, d, gy, tile, smem_raw);
                     break;
                 }
             }
@@ -170,6 +171,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
 struct fht_plan {
     int count = 0;
     int f32 = 0;
+    int sigma = 1;
     int n_segs = 0, total_items = 0;
     size_t table_bytes = 0, descs_off = 0, counters_off = 0, done_off = 0, levels_off = 0;
     size_t ws_bytes = 0, smem = 0;
@@ -309,6 +311,7 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
     if (!P) return FHT_ENOMEM;
     P->count = count;
     P->f32 = f32;
+    P->sigma = (q == 0 || q == 3) ? 1 : -1;
     P->n_segs = (int)segs.size();
     P->total_items = items;
     P->n_done = n_done;
@@ -362,7 +365,10 @@ fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void
         e = cudaMemsetAsync(ws + plan->counters_off, 0,
                             plan->levels_off - plan->counters_off, st);
     if (e != cudaSuccess) return FHT_ECUDA;
-    auto k = plan->f32 ? batched_forward_kernel<true> : batched_forward_kernel<false>;
+    auto k = plan->f32 ? (plan->sigma > 0 ? batched_forward_kernel<true, 1>
+                                          : batched_forward_kernel<true, -1>)
+                       : (plan->sigma > 0 ? batched_forward_kernel<false, 1>
+                                          : batched_forward_kernel<false, -1>);
     if (plan->smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
         if (e != cudaSuccess) return FHT_ECUDA;

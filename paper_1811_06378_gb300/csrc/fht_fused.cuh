@@ -289,10 +289,10 @@ __host__ __device__ inline TileGeom tile_geom(int MA, int MB, int n_a, int nwarp
 
 // Source row segment for block A: 8 buffer columns starting at i0 of buffer
 // row s, into v (buffer order).
-template <bool ADJ, typename Acc, typename SrcE>
+template <int SG, bool ADJ, typename Acc, typename SrcE>
 __device__ __forceinline__ void load_source(const PassDesc &d, int M, int S, int a, int s,
                                             int A_off, int i0, Acc (&v)[kV]) {
-    const int sg = d.sigma;
+    constexpr int sg = SG;
     const int p_first = A_off + sg * (i0 + a * s);
     const int lo = sg > 0 ? p_first : p_first - (kV - 1);
     const SrcE *base = reinterpret_cast<const SrcE *>(d.lo.ptr);
@@ -327,11 +327,11 @@ __device__ __forceinline__ void load_source(const PassDesc &d, int M, int S, int
 // Transposed image block for block A of the first pass (quadrants Q2, Q3):
 // rows s0..s0+RA-1 of the transposed image are image columns; the 8 buffer
 // columns are 8 image rows.
-template <int RA, typename Acc, typename SrcE>
+template <int SG, int RA, typename Acc, typename SrcE>
 __device__ __forceinline__ void load_source_transposed(const PassDesc &d, int M, int S,
                                                        int s0, int A_off, int i0,
                                                        Acc (&v)[RA][kV]) {
-    const int sg = d.sigma;
+    constexpr int sg = SG;
     const int p_first = A_off + sg * i0;
     const int lo = (sg > 0 ? p_first : p_first - (kV - 1)) - (sg > 0 ? 1 : 0);  // image row
     const int y0 = S * (1 << M) + s0;                                         // image column
@@ -363,15 +363,15 @@ struct Block {
 
 // Rare edge items (tile borders, image borders, wraps): per-row checked loads,
 // out of line.
-template <int RA, bool ADJ, typename Acc, typename SrcE>
+template <int SG, int RA, bool ADJ, typename Acc, typename SrcE>
 __device__ __noinline__ Block<Acc, RA> load_block_a_edge(const PassDesc &d, int M, int S, int a,
                                                          int s0, int A_off, int i0) {
     Block<Acc, RA> b;
     if (!ADJ && d.lo_image && d.transpose) {
-        load_source_transposed<RA, Acc, SrcE>(d, M, S, s0, A_off, i0, b.x);
+        load_source_transposed<SG, RA, Acc, SrcE>(d, M, S, s0, A_off, i0, b.x);
     } else {
 #pragma unroll
-        for (int r = 0; r < RA; ++r) load_source<ADJ, Acc, SrcE>(d, M, S, a, s0 + r, A_off, i0, b.x[r]);
+        for (int r = 0; r < RA; ++r) load_source<SG, ADJ, Acc, SrcE>(d, M, S, a, s0 + r, A_off, i0, b.x[r]);
     }
     return b;
 }
@@ -380,10 +380,10 @@ __device__ __noinline__ Block<Acc, RA> load_block_a_edge(const PassDesc &d, int 
 // Whether every row and every lane of the warp item (columns wbase ..
 // wbase + 255) lies inside the source is decided once, warp-uniformly; the
 // common interior case then issues all rows' loads without branches.
-template <int RA, bool ADJ, typename Acc, typename SrcE>
+template <int SG, int RA, bool ADJ, typename Acc, typename SrcE>
 __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, int a, int s0,
                                              int A_off, int wbase, int i0, Acc (&v)[RA][kV]) {
-    const int sg = d.sigma;
+    constexpr int sg = SG;
     const int splus = sg > 0 ? 1 : 0;
     // ascending source-column range [lo_min, hi_max) over the warp item
     int lo_min, hi_max;
@@ -411,7 +411,7 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
         interior = lo_min >= 0 && hi_max <= (ADJ ? d.W : d.lo.cols);
     }
     if (!interior) {
-        const Block<Acc, RA> b = load_block_a_edge<RA, ADJ, Acc, SrcE>(d, M, S, a, s0, A_off, i0);
+        const Block<Acc, RA> b = load_block_a_edge<SG, RA, ADJ, Acc, SrcE>(d, M, S, a, s0, A_off, i0);
 #pragma unroll
         for (int r = 0; r < RA; ++r)
 #pragma unroll
@@ -432,20 +432,34 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
             for (int k = 0; k < kV; ++k) v[r][k] = sg > 0 ? blk[k][r] : blk[kV - 1 - k][r];
         return;
     }
+    // row r of the block: one base pointer plus r strides; the column moves by
+    // sg*a per row (the shear) for intermediate levels
+    int64_t first_row, stride;
+    int lo0, dlo;
+    {
+        const int p_first = A_off + sg * (i0 + a * s0);
+        lo0 = sg > 0 ? p_first : p_first - (kV - 1);
+        if (d.lo_image) {
+            lo0 -= splus;
+            dlo = 0;
+            if constexpr (ADJ) {
+                first_row = (int64_t)d.src_row_base + (int64_t)d.src_row_dir * row0;
+                stride = (int64_t)d.src_row_dir * d.lo.pitch;
+            } else {
+                first_row = row0;
+                stride = d.lo.pitch;
+            }
+        } else {
+            first_row = ((int64_t)(S * (1 << M) + s0) << d.k0) + a;
+            stride = d.lo.pitch << d.k0;
+            dlo = sg * a;
+        }
+    }
+    const SrcE *p0 = base + first_row * d.lo.pitch;
 #pragma unroll
     for (int r = 0; r < RA; ++r) {
-        const int s = s0 + r;
-        const int p_first = A_off + sg * (i0 + a * s);
-        int lo = sg > 0 ? p_first : p_first - (kV - 1);
-        int64_t row;
-        if (d.lo_image) {
-            lo -= splus;
-            row = ADJ ? (int64_t)d.src_row_base + (int64_t)d.src_row_dir * (row0 + r) : row0 + r;
-        } else {
-            row = ((int64_t)(S * (1 << M) + s) << d.k0) + a;
-        }
-        load8_fast<SrcE, Acc>(base + row * d.lo.pitch, lo, v[r]);
-        if (sg < 0) reverse8(v[r]);
+        load8_fast<SrcE, Acc>(p0 + r * stride, lo0 + r * dlo, v[r]);
+        if constexpr (sg < 0) reverse8(v[r]);
     }
 }
 
@@ -457,10 +471,10 @@ struct DestCols {
     bool vec;     // the 8 land contiguously, in bounds and 16-byte aligned
 };
 
-template <typename Acc, typename DstE>
+template <int SG, typename Acc, typename DstE>
 __device__ __forceinline__ DestCols dest_cols(const PassDesc &d, int D, int i0) {
     DestCols c;
-    const int sg = d.sigma;
+    constexpr int sg = SG;
     const int p_first = D + sg * i0;
     c.lo = sg > 0 ? p_first : p_first - (kV - 1);
     if (!d.hi_final) {
@@ -503,10 +517,10 @@ __device__ __noinline__ void store_final_edge(const PassDesc &d, DstE *row, int 
 }
 
 // Store 8 buffer columns of level-k1 row hi_r (values in buffer order).
-template <typename Acc, typename DstE>
+template <int SG, typename Acc, typename DstE>
 __device__ __forceinline__ void store_dest(const PassDesc &d, const DestCols &c, int hi_r,
                                            const Acc (&v)[kV]) {
-    const int sg = d.sigma;
+    constexpr int sg = SG;
     Acc asc[kV];
 #pragma unroll
     for (int k = 0; k < kV; ++k) asc[k] = sg > 0 ? v[k] : v[kV - 1 - k];
@@ -530,6 +544,47 @@ __device__ __forceinline__ void store_dest(const PassDesc &d, const DestCols &c,
     store_final_edge<Acc, DstE>(d, row, t, c.lo, r);
 }
 
+// Store R consecutive level-k1 rows hi_r0.. of this lane's 8 columns: one base
+// pointer plus a stride per row; for the final level the rows outside
+// [t_first, t_last] (range / full-image maps) are skipped.
+template <int SG, int R, typename Acc, typename DstE>
+__device__ __forceinline__ void store_rows(const PassDesc &d, const DestCols &c, int hi_r0,
+                                           const Acc (&v)[R][kV]) {
+    DstE *base = reinterpret_cast<DstE *>(d.hi.ptr);
+    if (!d.hi_final) {
+        DstE *row = base + (int64_t)hi_r0 * d.hi.pitch;
+        const int64_t stride = d.hi.pitch;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            Acc asc[kV];
+#pragma unroll
+            for (int k = 0; k < kV; ++k) asc[k] = SG > 0 ? v[r][k] : v[r][kV - 1 - k];
+            if (c.vec) store8<DstE, Acc>(row + r * stride, c.lo, c.lo + kV, asc);
+            else store8<DstE, Acc>(row + r * stride, c.lo, d.hi.cols, asc);
+        }
+        return;
+    }
+    const int t0 = hi_r0;
+    const int r_lo = d.t_first - t0, r_hi = d.t_last - t0;   // rows r in [r_lo, r_hi] exist
+    DstE *row = base + ((int64_t)d.row_base + (int64_t)d.row_dir * t0) * d.hi.pitch;
+    const int64_t stride = (int64_t)d.row_dir * d.hi.pitch;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r < r_lo || r > r_hi) continue;
+        Acc asc[kV];
+#pragma unroll
+        for (int k = 0; k < kV; ++k) asc[k] = SG > 0 ? v[r][k] : v[r][kV - 1 - k];
+        if (c.vec) {
+            store8<DstE, Acc>(row + r * stride, c.X0, c.X0 + kV, asc);
+        } else {
+            Vec8<Acc> e;
+#pragma unroll
+            for (int k = 0; k < kV; ++k) e.x[k] = asc[k];
+            store_final_edge<Acc, DstE>(d, row + r * stride, t0 + r, c.lo, e);
+        }
+    }
+}
+
 // Final level of an adjoint: R consecutive output rows y0.. (image rows of the
 // (transposed) image) x this lane's 8 columns go to the image gradient,
 // cropped to dst_h x dst_w, transposed for the horizontal quadrants, added to
@@ -539,13 +594,13 @@ __device__ __forceinline__ E acc_store(E old, Acc v, bool acc) {
     return acc ? (E)Arith<Acc>::add((Acc)old, v) : (E)v;
 }
 
-template <int R, typename Acc, typename DstE>
+template <int SG, int R, typename Acc, typename DstE>
 __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int lo,
                                                   const Acc (&v)[R][kV]) {
     // columns p in [p_begin, p_begin + p_count) are exactly the image columns
     // X = p - sigma_plus*n < dst_w; a tile wider than W would otherwise reach
     // the same X again through the cyclic wrap
-    const int sg = d.sigma;
+    constexpr int sg = SG;
     const bool acc = d.accumulate != 0;
     const int p_lo = d.p_begin, p_hi = d.p_begin + d.p_count;
     const int X0 = lo - (sg > 0 ? d.n : 0);   // column of p = lo (valid when lo >= p_lo)
@@ -637,7 +692,7 @@ __device__ __forceinline__ bool tile_all_black(const PassDesc &d, int M, int a, 
 // ADJ selects the adjoint form at compile time (cyclic columns, row-mapped
 // gradient source, image-gradient destination) so the forward kernels carry
 // none of its code.
-template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int MA, int MB, int SG, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
 __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm) {
     constexpr int M = MA + MB, RA = 1 << MA, RB = 1 << MB;
     constexpr int PAD = TilePad<MidE>::kPad;
@@ -647,7 +702,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
     const int T = G.tile_out;
     const int S = gy / d.a_count, a = d.a_lo + gy % d.a_count;
     const int p0 = d.p_begin + tile * T;
-    const int sg = d.sigma;
+    constexpr int sg = SG;
     const int A_off = sg > 0 ? p0 - (1 << (d.k0 + M)) + (1 << d.k0) : p0 + T - 1;
     const int D = sg > 0 ? p0 : p0 + T - 1;
     const bool black = !ADJ && tile_all_black(d, M, a, p0, T);
@@ -658,7 +713,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             const int i0 = item * kWarpValid + lane * kV;
             Acc v[RA][kV];
             if (!black) {
-                load_block_a<RA, ADJ, Acc, SrcE>(d, M, S, a, 0, A_off, item * kWarpValid, i0, v);
+                load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, S, a, 0, A_off, item * kWarpValid, i0, v);
                 reg_butterfly<MA, Acc>(v);
             } else {
 #pragma unroll
@@ -667,13 +722,11 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                     for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
             }
             if (lane < kLanesValid && i0 < T) {
-                const DestCols dc = dest_cols<Acc, DstE>(d, D, i0);
+                const DestCols dc = dest_cols<SG, Acc, DstE>(d, D, i0);
                 if (ADJ && d.hi_final) {
-                    store_image_block<RA, Acc, DstE>(d, hi_row(d, M, S, a, 0), dc.lo, v);
+                    store_image_block<SG, RA, Acc, DstE>(d, hi_row(d, M, S, a, 0), dc.lo, v);
                 } else {
-#pragma unroll
-                    for (int c = 0; c < RA; ++c)
-                        store_dest<Acc, DstE>(d, dc, hi_row(d, M, S, a, c), v[c]);
+                    store_rows<SG, RA, Acc, DstE>(d, dc, hi_row(d, M, S, a, 0), v);
                 }
             }
         }
@@ -686,7 +739,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                 const int g = item % RB, wc = item / RB;
                 const int i0 = wc * kWarpValid + lane * kV;
                 Acc v[RA][kV];
-                load_block_a<RA, ADJ, Acc, SrcE>(d, M, S, a, g * RA, A_off, wc * kWarpValid, i0, v);
+                load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, S, a, g * RA, A_off, wc * kWarpValid, i0, v);
                 reg_butterfly<MA, Acc>(v);
                 if (lane < kLanesValid) {
                     const int pos = (8 + PAD) * (i0 >> 3);   // i0 is a multiple of 8
@@ -734,13 +787,11 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                     for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
             }
             if (lane < kLanesValid && i0 < T) {
-                const DestCols dc = dest_cols<Acc, DstE>(d, D, i0);
+                const DestCols dc = dest_cols<SG, Acc, DstE>(d, D, i0);
                 if (ADJ && d.hi_final) {
-                    store_image_block<RB, Acc, DstE>(d, hi_row(d, M, S, a, a2 * RB), dc.lo, v);
+                    store_image_block<SG, RB, Acc, DstE>(d, hi_row(d, M, S, a, a2 * RB), dc.lo, v);
                 } else {
-#pragma unroll
-                    for (int c = 0; c < RB; ++c)
-                        store_dest<Acc, DstE>(d, dc, hi_row(d, M, S, a, a2 * RB + c), v[c]);
+                    store_rows<SG, RB, Acc, DstE>(d, dc, hi_row(d, M, S, a, a2 * RB), v);
                 }
             }
         }

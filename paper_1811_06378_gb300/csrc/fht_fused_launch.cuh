@@ -35,17 +35,18 @@ inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t 
     return rd + wr;
 }
 
-template <int MA, int MB, typename Acc, typename SrcE, typename MidE, typename DstE>
+// SG is the pass's sign in buffer coordinates (+1 or -1), fixed at compile time.
+template <int MA, int MB, int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
 __global__ void __launch_bounds__(kFusedWarps * 32) fused_forward_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_forward_item<MA, MB, false, Acc, SrcE, MidE, DstE>(
+    fused_forward_item<MA, MB, SG, false, Acc, SrcE, MidE, DstE>(
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
 }
 
-template <int MA, int MB, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int MA, int MB, int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
 __global__ void __launch_bounds__(kFusedWarps * 32) fused_adjoint_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_forward_item<MA, MB, true, Acc, SrcE, MidE, DstE>(
+    fused_forward_item<MA, MB, SG, true, Acc, SrcE, MidE, DstE>(
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
 }
 
@@ -58,8 +59,13 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     size_t smem = MB == 0 ? 0 : (size_t)(1 << (MA + MB)) * G.pitch * sizeof(MidE);
     void (*k)(PassDesc);
-    if constexpr (ADJ) k = fused_adjoint_kernel<MA, MB, Acc, SrcE, MidE, DstE>;
-    else k = fused_forward_kernel<MA, MB, Acc, SrcE, MidE, DstE>;
+    if constexpr (ADJ) {
+        k = d.sigma > 0 ? fused_adjoint_kernel<MA, MB, 1, Acc, SrcE, MidE, DstE>
+                        : fused_adjoint_kernel<MA, MB, -1, Acc, SrcE, MidE, DstE>;
+    } else {
+        k = d.sigma > 0 ? fused_forward_kernel<MA, MB, 1, Acc, SrcE, MidE, DstE>
+                        : fused_forward_kernel<MA, MB, -1, Acc, SrcE, MidE, DstE>;
+    }
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
