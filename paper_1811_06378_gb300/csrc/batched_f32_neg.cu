@@ -1,0 +1,11 @@
+// batched_f32_neg.cu -- one instantiation of the persistent batched-forward
+// kernel (float, slope sign -).
+#include "fht_batched.cuh"
+
+namespace fht {
+namespace batched {
+
+Kernel kernel_f32_neg() { return batched_forward_kernel<true, -1>; }
+
+}  // namespace batched
+}  // namespace fht

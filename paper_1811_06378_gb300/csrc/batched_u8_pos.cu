@@ -1,0 +1,11 @@
+// batched_u8_pos.cu -- one instantiation of the persistent batched-forward
+// kernel (uint8 -> int32, slope sign +).
+#include "fht_batched.cuh"
+
+namespace fht {
+namespace batched {
+
+Kernel kernel_u8_pos() { return batched_forward_kernel<false, 1>; }
+
+}  // namespace batched
+}  // namespace fht

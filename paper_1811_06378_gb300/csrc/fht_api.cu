@@ -215,7 +215,7 @@ cudaError_t launch_forward(int M, const PassDesc &d, int acc, cudaStream_t st) {
 // shared memory (fewer CTAs per SM). Overridable for tuning through
 // FHT_TUNE="n_a_u16,n_a_wide".
 struct Tune {
-    int n_a_u16 = 2;    // first pass over uint8 images (uint16 shared tile)
+    int n_a_u16 = 1;    // first pass over uint8 images (uint16 shared tile)
     int n_a_wide = 1;   // 4-byte shared tiles
     Tune() {
         if (const char *e = getenv("FHT_TUNE")) {
@@ -355,18 +355,52 @@ __device__ void row_quadrant(const ShiftRows &m, int r, int *q, int *t, int *w_i
     else { *q = 3; *t = r - 2 * hp - wp + 3; *w_in = hp; }
 }
 
-template <typename T>
-__global__ void fhtshift_kernel(const T *in, T *out, int64_t in_pitch, int64_t out_pitch,
-                                ShiftRows m, int inverse) {
-    int r = blockIdx.x;
+// Rotates rows of 4-byte words: out[r][(x + s_r) mod W] = in[r][x]. One
+// group of `lanes` threads (a power of two, 32..kBlock) per row.
+//
+// Vector path (W and both pitches multiples of 4 words, both bases 16-byte
+// aligned): each thread writes aligned 16-byte output vectors. Output words
+// 4j..4j+3 come from source words x0..x0+3 (mod W), x0 = 4j - s (mod W); as W
+// is a multiple of 4 the row's wrap falls between aligned vectors, so those
+// words lie in the aligned source vectors a and a+1 (mod W/4), at the offset
+// o = (-s) mod 4, which is the same for the whole row.
+__global__ void __launch_bounds__(kBlock)
+    fhtshift_kernel(const uint32_t *in, uint32_t *out, int64_t in_pitch, int64_t out_pitch,
+                    ShiftRows m, int inverse, int rows, int lanes_log2, int vec) {
+    const int lanes = 1 << lanes_log2;
+    const int lane = threadIdx.x & (lanes - 1);
+    const int r = blockIdx.x * (kBlock >> lanes_log2) + (threadIdx.x >> lanes_log2);
+    if (r >= rows) return;
     int q, t, w_in;
     row_quadrant(m, r, &q, &t, &w_in);
-    int sigma = (q == 0 || q == 3) ? 1 : -1;
-    int s = fhtshift_amount(t, m.W, w_in, sigma);
-    if (inverse) s = m.W - s;
-    const T *src = in + (int64_t)r * in_pitch;
-    T *dst = out + (int64_t)r * out_pitch;
-    for (int x = threadIdx.x; x < m.W; x += blockDim.x) {
+    const int sigma = (q == 0 || q == 3) ? 1 : -1;
+    int s = fhtshift_amount(t, m.W, w_in, sigma);   // in [0, W)
+    if (inverse) s = m.W - s;                         // in (0, W]
+    if (vec) {
+        const int nv = m.W >> 2;
+        const uint4 *src = reinterpret_cast<const uint4 *>(in + (int64_t)r * in_pitch);
+        uint4 *dst = reinterpret_cast<uint4 *>(out + (int64_t)r * out_pitch);
+        const int o = (-s) & 3;
+        const int sv = (s + o) >> 2;   // x0 = 4 (j - sv) + o, sv in [0, nv]
+#pragma unroll 4
+        for (int j = lane; j < nv; j += lanes) {
+            int a = j - sv;
+            if (a < 0) a += nv;
+            const uint4 v0 = __ldg(src + a);
+            uint4 res = v0;
+            if (o != 0) {
+                const uint4 v1 = __ldg(src + (a + 1 == nv ? 0 : a + 1));
+                if (o == 1) res = make_uint4(v0.y, v0.z, v0.w, v1.x);
+                else if (o == 2) res = make_uint4(v0.z, v0.w, v1.x, v1.y);
+                else res = make_uint4(v0.w, v1.x, v1.y, v1.z);
+            }
+            dst[j] = res;
+        }
+        return;
+    }
+    const uint32_t *src = in + (int64_t)r * in_pitch;
+    uint32_t *dst = out + (int64_t)r * out_pitch;
+    for (int x = lane; x < m.W; x += lanes) {
         int xo = x + s;
         if (xo >= m.W) xo -= m.W;
         dst[xo] = src[x];
@@ -574,16 +608,21 @@ fht_status fhtshift(const void *in, void *out, fht_dtype dtype, int h, int w,
         return FHT_EINVAL;
     }
     if (in_pitch < m.W || out_pitch < m.W) return FHT_EINVAL;
-    dim3 grid(rows);
+    const bool vec = m.W % 4 == 0 && in_pitch % 4 == 0 && out_pitch % 4 == 0 &&
+                     reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(out) % 16 == 0;
+    const int units = vec ? m.W / 4 : m.W;   // per row, one thread each
+    int lanes_log2 = 5;
+    while ((1 << lanes_log2) < units && (1 << lanes_log2) < kBlock) ++lanes_log2;
+    const int rows_per_block = kBlock >> lanes_log2;
+    dim3 grid((rows + rows_per_block - 1) / rows_per_block);
     cudaStream_t st = (cudaStream_t)stream;
     LaunchScope scope(dtype == FHT_I32 ? "fhtshift_i32" : "fhtshift_f32", st,
                       2.0 * rows * m.W * 4.0);
-    if (dtype == FHT_I32)
-        fhtshift_kernel<int32_t><<<grid, kBlock, 0, st>>>((const int32_t *)in, (int32_t *)out,
-                                                          in_pitch, out_pitch, m, inverse);
-    else
-        fhtshift_kernel<float><<<grid, kBlock, 0, st>>>((const float *)in, (float *)out,
-                                                        in_pitch, out_pitch, m, inverse);
+    // both types are moved as 4-byte words
+    fhtshift_kernel<<<grid, kBlock, 0, st>>>(static_cast<const uint32_t *>(in),
+                                             static_cast<uint32_t *>(out), in_pitch, out_pitch,
+                                             m, inverse, rows, lanes_log2, vec ? 1 : 0);
     scope.done();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

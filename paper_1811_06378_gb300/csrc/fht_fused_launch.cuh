@@ -9,7 +9,13 @@
 
 namespace fht {
 
-constexpr int kFusedWarps = 8;
+#ifndef FHT_FUSED_WARPS
+#define FHT_FUSED_WARPS 8
+#endif
+// Warps per CTA of the fused pass; CTAs per SM are sized to 16 warps.
+constexpr int kFusedWarps = FHT_FUSED_WARPS;
+// Largest dynamic shared memory one block may opt in to on sm_100-class parts.
+constexpr size_t kMaxTileSmem = 227 * 1024;
 
 // Bytes a pass must read and write at least: its source level as stored
 // (image, or compact intermediate rows of the launched groups) and its
@@ -37,14 +43,14 @@ inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t 
 
 // SG is the pass's sign in buffer coordinates (+1 or -1), fixed at compile time.
 template <int MA, int MB, int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
-__global__ void __launch_bounds__(kFusedWarps * 32) fused_forward_kernel(PassDesc d) {
+__global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps) fused_forward_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_forward_item<MA, MB, SG, false, Acc, SrcE, MidE, DstE>(
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
 }
 
 template <int MA, int MB, int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
-__global__ void __launch_bounds__(kFusedWarps * 32) fused_adjoint_kernel(PassDesc d) {
+__global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps) fused_adjoint_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_forward_item<MA, MB, SG, true, Acc, SrcE, MidE, DstE>(
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
@@ -53,11 +59,19 @@ __global__ void __launch_bounds__(kFusedWarps * 32) fused_adjoint_kernel(PassDes
 template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
 cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     TileGeom G = tile_geom(MA, MB, d.n_a, kFusedWarps, TilePad<MidE>::kPad);
+    size_t smem = MB == 0 ? 0 : (size_t)(1 << (MA + MB)) * G.pitch * sizeof(MidE);
+    // A tuned tile width that does not fit one block's shared memory is
+    // narrowed until it does.
+    while (smem > kMaxTileSmem && d.n_a > 1) {
+        d.n_a--;
+        G = tile_geom(MA, MB, d.n_a, kFusedWarps, TilePad<MidE>::kPad);
+        smem = (size_t)(1 << (MA + MB)) * G.pitch * sizeof(MidE);
+    }
+    if (smem > kMaxTileSmem) return cudaErrorInvalidConfiguration;
     d.tile_w = G.tile_out;
     d.tiles = (d.p_count + G.tile_out - 1) / G.tile_out;
     dim3 grid(d.tiles, d.s_count * d.a_count);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    size_t smem = MB == 0 ? 0 : (size_t)(1 << (MA + MB)) * G.pitch * sizeof(MidE);
     void (*k)(PassDesc);
     if constexpr (ADJ) {
         k = d.sigma > 0 ? fused_adjoint_kernel<MA, MB, 1, Acc, SrcE, MidE, DstE>

@@ -141,6 +141,29 @@ def test_fhtshift_standalone(fht, h, w):
         assert (Sf == S.astype(np.float32)).all()
 
 
+def test_fhtshift_pitches_and_alignment(fht):
+    """Rows move as 16-byte vectors when the row width, both pitches and both
+    base addresses allow it, else word by word: every combination gives the
+    oracle's rows."""
+    h, w = 300, 500
+    img = edges_and_lines(h, w, seed=8)
+    want = as_i32(O.fhtshift_full(O.full(img), h, w))
+    F = fht.full_quadrants(dev(img))
+    R, W = F.shape
+    assert W % 4 == 0
+    for in_extra, in_off, out_extra, out_off in [(0, 0, 4, 0), (3, 0, 0, 0), (4, 1, 0, 0),
+                                                 (0, 0, 8, 3), (5, 2, 7, 1)]:
+        src_buf = torch.zeros((R, W + in_extra + in_off), dtype=torch.int32, device="cuda")
+        src = src_buf[:, in_off:in_off + W]
+        src.copy_(F)
+        dst_buf = torch.full((R, W + out_extra + out_off), -5, dtype=torch.int32, device="cuda")
+        dst = dst_buf[:, out_off:out_off + W]
+        fht.fhtshift(src, h, w, fht.LAYOUT_FULL, out=dst)
+        got = host(dst_buf)
+        assert (got[:, out_off:out_off + W] == want).all(), (in_extra, in_off, out_extra, out_off)
+        assert (got[:, :out_off] == -5).all() and (got[:, out_off + W:] == -5).all()
+
+
 @pytest.mark.parametrize("h,w", [(1, 1), (3, 5), (32, 32), (37, 53), (200, 129)])
 def test_adjoint_quadrant(fht, h, w):
     rng = np.random.default_rng(h * w)

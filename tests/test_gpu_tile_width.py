@@ -1,0 +1,53 @@
+"""Tile width of the fused passes: any FHT_TUNE setting gives the same result.
+
+FHT_TUNE="a,b" sets how many warp-widths of source columns one tile's first
+block of levels covers (a: first passes over uint8 images, whose shared tile
+holds uint16; b: tiles of 4-byte values). Wider tiles re-read less of the
+halo but need more shared memory; a width whose tile does not fit one block's
+shared memory is narrowed at launch. The setting is read when the library
+loads, so each width runs in a child process and its result is compared bit
+for bit with the oracle."""
+
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import sys
+import numpy as np
+import torch
+import paper_1811_06378_gb300 as fht
+from workloads import edges_and_lines, random_image
+img = edges_and_lines(1500, 1100, seed=21)
+f = random_image(700, 900, "f32", seed=22)
+out = [fht.forward(torch.from_numpy(img).cuda(), q).cpu().numpy() for q in range(4)]
+out += [fht.forward(torch.from_numpy(f).cuda(), q, acc=torch.float32).cpu().numpy()
+        for q in (0, 2)]
+np.savez(sys.argv[1], *out)
+"""
+
+
+@pytest.mark.parametrize("tune", ["1,1", "3,3", "2,2"])
+def test_tile_width_setting_is_bit_exact(tune, tmp_path):
+    import oracle as O
+    from workloads import edges_and_lines, random_image
+    path = str(tmp_path / "out.npz")
+    env = dict(os.environ, FHT_TUNE=tune, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", CHILD, path], env=env, cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = np.load(path)
+    img = edges_and_lines(1500, 1100, seed=21)
+    f = random_image(700, 900, "f32", seed=22)
+    for q in range(4):
+        want = O.quadrant(img, q).astype(np.int64).astype(np.int32)
+        assert (got[f"arr_{q}"] == want).all(), (tune, q)
+    for i, q in enumerate((0, 2)):
+        assert (got[f"arr_{4 + i}"] == O.quadrant(f, q, kind="f32")).all(), (tune, q)
