@@ -44,23 +44,24 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     return v;
 }
 
-template <int MA, int MB, int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
 __device__ __forceinline__ void run_item(const PassDesc &d, int gy, int tile, unsigned char *sm) {
-    fused_forward_item<MA, MB, SG, false, Acc, SrcE, MidE, DstE>(d, gy, tile,
-                                                                 reinterpret_cast<MidE *>(sm));
+    fused_forward_item<MA, MB, SG, false, FIN, Acc, SrcE, MidE, DstE>(
+        d, gy, tile, reinterpret_cast<MidE *>(sm));
 }
 
-template <int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int SG, bool FIN, typename Acc, typename SrcE, typename MidE, typename DstE>
 __device__ __forceinline__ void run_item_m(int m, const PassDesc &d, int gy, int tile,
                                            unsigned char *sm) {
     switch (m) {
-    case 0: run_item<0, 0, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 1: run_item<1, 0, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 2: run_item<2, 0, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 3: run_item<3, 0, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 4: run_item<3, 1, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 5: run_item<3, 2, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    default: run_item<3, 3, SG, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 0: run_item<0, 0, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 1: run_item<1, 0, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 2: run_item<2, 0, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 3: run_item<3, 0, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 4: run_item<3, 1, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 5: run_item<3, 2, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    default: run_item<3, 3, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
     }
 }
 
@@ -132,17 +133,25 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
             const int local = item - sg.item_begin;
             const int gy = local / sg.tiles, tile = local - gy * sg.tiles;
             if constexpr (F32) {
-                run_item_m<SG, float, float, float, float>(sg.m, d, gy, tile, smem_raw);
+                if (d.hi_final)
+                    run_item_m<SG, true, float, float, float, float>(sg.m, d, gy, tile, smem_raw);
+                else
+                    run_item_m<SG, false, float, float, float, float>(sg.m, d, gy, tile, smem_raw);
             } else {
+                // a uint8 image is finished in one pass or goes to a uint16
+                // level; a uint16 level's pass is the last (two passes at most)
                 switch (sg.variant) {
                 case kVarU8Final:
-                    run_item_m<SG, int32_t, uint8_t, uint16_t, int32_t>(sg.m, d, gy, tile, smem_raw);
+                    run_item_m<SG, true, int32_t, uint8_t, uint16_t, int32_t>(sg.m, d, gy, tile,
+                                                                             smem_raw);
                     break;
                 case kVarU8Level:
-                    run_item_m<SG, int32_t, uint8_t, uint16_t, uint16_t>(sg.m, d, gy, tile, smem_raw);
+                    run_item_m<SG, false, int32_t, uint8_t, uint16_t, uint16_t>(sg.m, d, gy, tile,
+                                                                               smem_raw);
                     break;
                 default:
-                    run_item_m<SG, int32_t, uint16_t, int32_t, int32_t>(sg.m, d, gy, tile, smem_raw);
+                    run_item_m<SG, true, int32_t, uint16_t, int32_t, int32_t>(sg.m, d, gy, tile,
+                                                                             smem_raw);
                     break;
                 }
             }

@@ -63,6 +63,11 @@ __device__ __forceinline__ Acc from_word(uint32_t w, std::false_type) {
     return (Acc)(int32_t)w;
 }
 
+// Low halves of lo and hi as one word (lo in bits 0..15): one byte permute.
+__device__ __forceinline__ uint32_t pack_u16x2(uint32_t lo, uint32_t hi) {
+    return __byte_perm(lo, hi, 0x5410u);
+}
+
 // Eight values passed by value to and from the out-of-line edge paths.
 template <typename Acc>
 struct Vec8 {
@@ -109,9 +114,9 @@ __device__ __forceinline__ void load8_fast(const E *row, int lo, Acc (&v)[kV]) {
         const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)(delta & 3);
         const uint32_t b0 = __byte_perm(u0, u1, sel), b1 = __byte_perm(u1, u2, sel);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[k] = (Acc)(int32_t)((b0 >> (8 * k)) & 0xffu);
-            v[k + 4] = (Acc)(int32_t)((b1 >> (8 * k)) & 0xffu);
+        for (int k = 0; k < 4; ++k) {   // byte k, zero-extended: one byte permute each
+            v[k] = (Acc)(int32_t)__byte_perm(b0, 0u, 0x4440u | k);
+            v[k + 4] = (Acc)(int32_t)__byte_perm(b1, 0u, 0x4440u | k);
         }
     } else if constexpr (sizeof(E) == 2) {
         const int delta = (int)((a & 15) >> 1);
@@ -196,10 +201,10 @@ __device__ __forceinline__ void store8(E *row, int lo, int cols, const Acc (&v)[
     if (lo >= 0 && lo + kV <= cols && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
         if constexpr (sizeof(E) == 2) {
             uint4 q;
-            q.x = (uint32_t)(uint16_t)v[0] | ((uint32_t)(uint16_t)v[1] << 16);
-            q.y = (uint32_t)(uint16_t)v[2] | ((uint32_t)(uint16_t)v[3] << 16);
-            q.z = (uint32_t)(uint16_t)v[4] | ((uint32_t)(uint16_t)v[5] << 16);
-            q.w = (uint32_t)(uint16_t)v[6] | ((uint32_t)(uint16_t)v[7] << 16);
+            q.x = pack_u16x2((uint32_t)v[0], (uint32_t)v[1]);
+            q.y = pack_u16x2((uint32_t)v[2], (uint32_t)v[3]);
+            q.z = pack_u16x2((uint32_t)v[4], (uint32_t)v[5]);
+            q.w = pack_u16x2((uint32_t)v[6], (uint32_t)v[7]);
             *reinterpret_cast<uint4 *>(p) = q;
         } else {
             using V4 = typename std::conditional<std::is_same<E, float>::value, float4, int4>::type;
@@ -471,18 +476,18 @@ struct DestCols {
     bool vec;     // the 8 land contiguously, in bounds and 16-byte aligned
 };
 
-template <int SG, typename Acc, typename DstE>
+template <int SG, bool FIN, typename Acc, typename DstE>
 __device__ __forceinline__ DestCols dest_cols(const PassDesc &d, int D, int i0) {
     DestCols c;
     constexpr int sg = SG;
     const int p_first = D + sg * i0;
     c.lo = sg > 0 ? p_first : p_first - (kV - 1);
-    if (!d.hi_final) {
+    if constexpr (!FIN) {
         c.X0 = c.lo;
         c.vec = c.lo >= 0 && c.lo + kV <= d.hi.cols && (d.hi.pitch & 7) == 0 &&
                 (c.lo & 7) == 0 && ((reinterpret_cast<uintptr_t>(d.hi.ptr) & 15) == 0);
         return c;
-    }
+    } else {
     // column of p: X = p - sigma_plus*n (mod W); fhtshift handled per row
     int X0 = c.lo - (sg > 0 ? d.n : 0);
     if (X0 < 0) X0 += d.W;
@@ -490,6 +495,7 @@ __device__ __forceinline__ DestCols dest_cols(const PassDesc &d, int D, int i0) 
     c.vec = !d.shift_on && c.lo >= 0 && c.lo + kV <= d.W && X0 + kV <= d.W && (X0 & 3) == 0 &&
             (d.hi.pitch & 3) == 0 && ((reinterpret_cast<uintptr_t>(d.hi.ptr) & 15) == 0);
     return c;
+    }
 }
 
 // Final-level store of 8 ascending columns p = lo.. of slope t when they do not
@@ -516,42 +522,14 @@ __device__ __noinline__ void store_final_edge(const PassDesc &d, DstE *row, int 
     }
 }
 
-// Store 8 buffer columns of level-k1 row hi_r (values in buffer order).
-template <int SG, typename Acc, typename DstE>
-__device__ __forceinline__ void store_dest(const PassDesc &d, const DestCols &c, int hi_r,
-                                           const Acc (&v)[kV]) {
-    constexpr int sg = SG;
-    Acc asc[kV];
-#pragma unroll
-    for (int k = 0; k < kV; ++k) asc[k] = sg > 0 ? v[k] : v[kV - 1 - k];
-    DstE *base = reinterpret_cast<DstE *>(d.hi.ptr);
-    if (!d.hi_final) {
-        DstE *row = base + (int64_t)hi_r * d.hi.pitch;
-        if (c.vec) store8<DstE, Acc>(row, c.lo, c.lo + kV, asc);
-        else store8<DstE, Acc>(row, c.lo, d.hi.cols, asc);
-        return;
-    }
-    const int t = hi_r;
-    if (t < d.t_first || t > d.t_last) return;
-    DstE *row = base + ((int64_t)d.row_base + (int64_t)d.row_dir * t) * d.hi.pitch;
-    if (c.vec) {
-        store8<DstE, Acc>(row, c.X0, c.X0 + kV, asc);
-        return;
-    }
-    Vec8<Acc> r;
-#pragma unroll
-    for (int k = 0; k < kV; ++k) r.x[k] = asc[k];
-    store_final_edge<Acc, DstE>(d, row, t, c.lo, r);
-}
-
 // Store R consecutive level-k1 rows hi_r0.. of this lane's 8 columns: one base
 // pointer plus a stride per row; for the final level the rows outside
 // [t_first, t_last] (range / full-image maps) are skipped.
-template <int SG, int R, typename Acc, typename DstE>
+template <int SG, bool FIN, int R, typename Acc, typename DstE>
 __device__ __forceinline__ void store_rows(const PassDesc &d, const DestCols &c, int hi_r0,
                                            const Acc (&v)[R][kV]) {
     DstE *base = reinterpret_cast<DstE *>(d.hi.ptr);
-    if (!d.hi_final) {
+    if constexpr (!FIN) {
         DstE *row = base + (int64_t)hi_r0 * d.hi.pitch;
         const int64_t stride = d.hi.pitch;
 #pragma unroll
@@ -563,7 +541,7 @@ __device__ __forceinline__ void store_rows(const PassDesc &d, const DestCols &c,
             else store8<DstE, Acc>(row + r * stride, c.lo, d.hi.cols, asc);
         }
         return;
-    }
+    } else {
     const int t0 = hi_r0;
     const int r_lo = d.t_first - t0, r_hi = d.t_last - t0;   // rows r in [r_lo, r_hi] exist
     DstE *row = base + ((int64_t)d.row_base + (int64_t)d.row_dir * t0) * d.hi.pitch;
@@ -582,6 +560,7 @@ __device__ __forceinline__ void store_rows(const PassDesc &d, const DestCols &c,
             for (int k = 0; k < kV; ++k) e.x[k] = asc[k];
             store_final_edge<Acc, DstE>(d, row + r * stride, t0 + r, c.lo, e);
         }
+    }
     }
 }
 
@@ -678,7 +657,7 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
 // (final level only: slopes t in [a*2^M, a*2^M + 2^M - 1])
 __device__ __forceinline__ bool tile_all_black(const PassDesc &d, int M, int a, int p0,
                                                int tile_out) {
-    if (!d.hi_final || d.cyclic) return false;
+    if (d.cyclic) return false;
     const int t_max = (a << M) + (1 << M) - 1;
     const int lo = p0, hi = p0 + tile_out;   // [lo, hi) in p
     if (d.sigma > 0) {
@@ -691,8 +670,11 @@ __device__ __forceinline__ bool tile_all_black(const PassDesc &d, int M, int a, 
 
 // ADJ selects the adjoint form at compile time (cyclic columns, row-mapped
 // gradient source, image-gradient destination) so the forward kernels carry
-// none of its code.
-template <int MA, int MB, int SG, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
+// none of its code; FIN likewise selects the final level's destination (the
+// caller's layout) over an intermediate level, so each kernel holds one store
+// path.
+template <int MA, int MB, int SG, bool ADJ, bool FIN, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
 __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm) {
     constexpr int M = MA + MB, RA = 1 << MA, RB = 1 << MB;
     constexpr int PAD = TilePad<MidE>::kPad;
@@ -705,7 +687,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
     constexpr int sg = SG;
     const int A_off = sg > 0 ? p0 - (1 << (d.k0 + M)) + (1 << d.k0) : p0 + T - 1;
     const int D = sg > 0 ? p0 : p0 + T - 1;
-    const bool black = !ADJ && tile_all_black(d, M, a, p0, T);
+    const bool black = !ADJ && FIN && tile_all_black(d, M, a, p0, T);
 
     if constexpr (MB == 0) {
         // single register block: source -> registers -> destination
@@ -722,11 +704,11 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                     for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
             }
             if (lane < kLanesValid && i0 < T) {
-                const DestCols dc = dest_cols<SG, Acc, DstE>(d, D, i0);
-                if (ADJ && d.hi_final) {
+                const DestCols dc = dest_cols<SG, FIN, Acc, DstE>(d, D, i0);
+                if constexpr (ADJ && FIN) {
                     store_image_block<SG, RA, Acc, DstE>(d, hi_row(d, M, S, a, 0), dc.lo, v);
                 } else {
-                    store_rows<SG, RA, Acc, DstE>(d, dc, hi_row(d, M, S, a, 0), v);
+                    store_rows<SG, FIN, RA, Acc, DstE>(d, dc, hi_row(d, M, S, a, 0), v);
                 }
             }
         }
@@ -750,8 +732,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                             uint32_t *w = reinterpret_cast<uint32_t *>(row);
 #pragma unroll
                             for (int k = 0; k < kV / 2; ++k)
-                                w[k] = (uint32_t)(uint16_t)v[c][2 * k] |
-                                       ((uint32_t)(uint16_t)v[c][2 * k + 1] << 16);
+                                w[k] = pack_u16x2((uint32_t)v[c][2 * k], (uint32_t)v[c][2 * k + 1]);
                         } else {
 #pragma unroll
                             for (int k = 0; k < kV; ++k) row[k] = (MidE)v[c][k];
@@ -787,11 +768,11 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                     for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
             }
             if (lane < kLanesValid && i0 < T) {
-                const DestCols dc = dest_cols<SG, Acc, DstE>(d, D, i0);
-                if (ADJ && d.hi_final) {
+                const DestCols dc = dest_cols<SG, FIN, Acc, DstE>(d, D, i0);
+                if constexpr (ADJ && FIN) {
                     store_image_block<SG, RB, Acc, DstE>(d, hi_row(d, M, S, a, a2 * RB), dc.lo, v);
                 } else {
-                    store_rows<SG, RB, Acc, DstE>(d, dc, hi_row(d, M, S, a, a2 * RB), v);
+                    store_rows<SG, FIN, RB, Acc, DstE>(d, dc, hi_row(d, M, S, a, a2 * RB), v);
                 }
             }
         }

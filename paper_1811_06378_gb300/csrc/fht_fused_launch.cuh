@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdio>
+#include <type_traits>
 
 #include "fht_fused.cuh"
 #include "fht_host.h"
@@ -41,19 +42,46 @@ inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t 
     return rd + wr;
 }
 
-// SG is the pass's sign in buffer coordinates (+1 or -1), fixed at compile time.
-template <int MA, int MB, int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
-__global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps) fused_forward_kernel(PassDesc d) {
+// SG is the pass's sign in buffer coordinates (+1 or -1) and FIN whether it
+// writes the final level, both fixed at compile time.
+template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
+__global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
+    fused_forward_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_forward_item<MA, MB, SG, false, Acc, SrcE, MidE, DstE>(
+    fused_forward_item<MA, MB, SG, false, FIN, Acc, SrcE, MidE, DstE>(
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
 }
 
-template <int MA, int MB, int SG, typename Acc, typename SrcE, typename MidE, typename DstE>
-__global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps) fused_adjoint_kernel(PassDesc d) {
+template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
+__global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
+    fused_adjoint_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_forward_item<MA, MB, SG, true, Acc, SrcE, MidE, DstE>(
+    fused_forward_item<MA, MB, SG, true, FIN, Acc, SrcE, MidE, DstE>(
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
+}
+
+// Which final-level flags a type combination can take: uint16 is only ever an
+// intermediate level, and a uint8 image goes to int32 only in a single
+// (final) pass.
+template <bool ADJ, typename SrcE, typename DstE>
+struct FinCases {
+    static constexpr bool kLevel = !(!ADJ && std::is_same<SrcE, uint8_t>::value &&
+                                     std::is_same<DstE, int32_t>::value);
+    static constexpr bool kFinal = !std::is_same<DstE, uint16_t>::value;
+};
+
+template <int MA, int MB, bool ADJ, bool FIN, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
+void (*fused_kernel_ptr(int sigma))(PassDesc) {
+    if constexpr (ADJ) {
+        return sigma > 0 ? fused_adjoint_kernel<MA, MB, 1, FIN, Acc, SrcE, MidE, DstE>
+                         : fused_adjoint_kernel<MA, MB, -1, FIN, Acc, SrcE, MidE, DstE>;
+    } else {
+        return sigma > 0 ? fused_forward_kernel<MA, MB, 1, FIN, Acc, SrcE, MidE, DstE>
+                         : fused_forward_kernel<MA, MB, -1, FIN, Acc, SrcE, MidE, DstE>;
+    }
 }
 
 template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
@@ -72,14 +100,14 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     d.tiles = (d.p_count + G.tile_out - 1) / G.tile_out;
     dim3 grid(d.tiles, d.s_count * d.a_count);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    void (*k)(PassDesc);
-    if constexpr (ADJ) {
-        k = d.sigma > 0 ? fused_adjoint_kernel<MA, MB, 1, Acc, SrcE, MidE, DstE>
-                        : fused_adjoint_kernel<MA, MB, -1, Acc, SrcE, MidE, DstE>;
+    using FC = FinCases<ADJ, SrcE, DstE>;
+    void (*k)(PassDesc) = nullptr;
+    if (d.hi_final) {
+        if constexpr (FC::kFinal) k = fused_kernel_ptr<MA, MB, ADJ, true, Acc, SrcE, MidE, DstE>(d.sigma);
     } else {
-        k = d.sigma > 0 ? fused_forward_kernel<MA, MB, 1, Acc, SrcE, MidE, DstE>
-                        : fused_forward_kernel<MA, MB, -1, Acc, SrcE, MidE, DstE>;
+        if constexpr (FC::kLevel) k = fused_kernel_ptr<MA, MB, ADJ, false, Acc, SrcE, MidE, DstE>(d.sigma);
     }
+    if (!k) return cudaErrorInvalidValue;   // a type combination no plan produces
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
