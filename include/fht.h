@@ -240,6 +240,18 @@ fht_status fht_batched_test_hooks(fht_plan *plan, long long wait_budget_cycles, 
 
 void fht_plan_destroy(fht_plan *plan);
 
+/* Device status of the single-image transforms (fht_forward,
+ * fht_forward_range, fht_full_quadrants, fht_adjoint and fht_forward_static)
+ * when their two-block passes run as persistent pipelined kernels (set
+ * FHT_PIPE=1 in the environment before the library loads; off by default),
+ * whose two warp groups hand shared tiles to each other through bounded
+ * waits. Without it the status is always FHT_OK. Waits for every launch
+ * issued so far in this process, then returns FHT_ETIMEOUT if any such wait
+ * ran out of its clock budget (about a second; the launch then ended early
+ * and its output is incomplete) and resets the count, else FHT_OK; FHT_ECUDA
+ * if the device could not be synchronised. Not in the paper. */
+fht_status fht_device_status(void);
+
 /* ------------------------------------------------------------ profiling
  * Kernel-level timing for benchmarks; normal use never needs it. Not in the
  * paper. While profiling is on, every kernel launch made by this library is

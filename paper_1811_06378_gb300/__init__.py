@@ -23,7 +23,8 @@ __all__ = [
     "Q0", "Q1", "Q2", "Q3", "LAYOUT_QUADRANT", "LAYOUT_FULL", "FHTError", "lib",
     "query_shape", "full_shape", "full_row_to_quadrant", "angle_to_slopes",
     "workspace_size", "forward", "forward_range", "full_quadrants", "fhtshift",
-    "adjoint", "FHTFunction", "profile_begin", "profile_end", "launch_count", "BatchPlan",
+    "adjoint", "FHTFunction", "profile_begin", "profile_end", "launch_count", "device_status",
+    "BatchPlan", "FHT_OK", "FHT_ETIMEOUT",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -31,6 +32,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfht.so")
 
 Q0, Q1, Q2, Q3 = 0, 1, 2, 3
 LAYOUT_QUADRANT, LAYOUT_FULL = 0, 1
+FHT_OK, FHT_ETIMEOUT = 0, 5
 _U8, _I32, _F32 = 0, 1, 2
 _DTYPE = {torch.uint8: _U8, torch.int32: _I32, torch.float32: _F32}
 
@@ -70,6 +72,7 @@ def _load() -> ctypes.CDLL:
         "fht_profile_begin": (i, []),
         "fht_profile_end": (i, [vp, i, ip]),
         "fht_launch_count": (ctypes.c_longlong, []),
+        "fht_device_status": (ctypes.c_int, []),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -360,6 +363,12 @@ def profile_end() -> dict[str, tuple[int, float, float]]:
 def launch_count() -> int:
     """Kernel launches issued by the library since it was loaded."""
     return int(lib.fht_launch_count())
+
+
+def device_status() -> int:
+    """Wait for the device; FHT_ETIMEOUT if a pipelined pass ran out of its
+    wait budget since the last call (the count is reset), else FHT_OK."""
+    return int(lib.fht_device_status())
 
 
 class FHTFunction(torch.autograd.Function):

@@ -213,10 +213,14 @@ cudaError_t launch_forward(int M, const PassDesc &d, int acc, cudaStream_t st) {
 
 // Block-A warp-columns per tile: wider tiles compute less halo but need more
 // shared memory (fewer CTAs per SM). Overridable for tuning through
-// FHT_TUNE="n_a_u16,n_a_wide".
+// FHT_TUNE="n_a_u16,n_a_wide"; FHT_PIPE=1 runs two-block passes as the
+// persistent warp-specialised pipeline instead of one item per CTA. The
+// pipeline is off by default: block B costs about 1.5x block A, so its
+// consumer warps bound it (4096^2 final int32 pass: 87 us against 72 us).
 struct Tune {
     int n_a_u16 = 1;    // first pass over uint8 images (uint16 shared tile)
     int n_a_wide = 1;   // 4-byte shared tiles
+    bool pipe = false;
     Tune() {
         if (const char *e = getenv("FHT_TUNE")) {
             int a = 0, b = 0;
@@ -225,9 +229,42 @@ struct Tune {
                 n_a_wide = b;
             }
         }
+        if (const char *e = getenv("FHT_PIPE")) pipe = e[0] == '1' && e[1] == 0;
     }
 };
 const Tune g_tune;
+
+std::mutex &counter_mu() {
+    static std::mutex mu;
+    return mu;
+}
+std::vector<unsigned int (*)()> &counter_fns() {
+    static std::vector<unsigned int (*)()> fns;
+    return fns;
+}
+
+}  // namespace
+
+namespace fht {
+
+bool pipe_enabled() { return g_tune.pipe; }
+
+bool register_device_counter(unsigned int (*read_and_reset)()) {
+    std::lock_guard<std::mutex> lk(counter_mu());
+    counter_fns().push_back(read_and_reset);
+    return true;
+}
+
+unsigned int read_device_counters() {
+    std::lock_guard<std::mutex> lk(counter_mu());
+    unsigned int n = 0;
+    for (auto f : counter_fns()) n += f();
+    return n;
+}
+
+}  // namespace fht
+
+namespace {
 
 // First passes over uint8 images keep their shared tile in uint16.
 bool acc_is_u16_mid(const QuadPlan &P, int p) { return p == 0 && P.in_elem == kU8 && P.acc_elem == kI32; }
@@ -669,6 +706,14 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
         if (s != FHT_OK) return s;
     }
     return FHT_OK;
+}
+
+fht_status fht_device_status(void) {
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        g_last_cuda_error = (int)cudaGetLastError();
+        return FHT_ECUDA;
+    }
+    return read_device_counters() ? FHT_ETIMEOUT : FHT_OK;
 }
 
 fht_status fht_profile_begin(void) {

@@ -668,6 +668,112 @@ __device__ __forceinline__ bool tile_all_black(const PassDesc &d, int M, int a, 
     return lo >= d.black_wc + t_max;
 }
 
+// Where one (group, tile) item of a pass sits: its group (S, a), first
+// output column p0, the buffer column offsets of its source (A_off) and
+// destination (D), and whether the whole tile is black (all zero).
+struct ItemPos {
+    int S, a, p0, A_off, D;
+    bool black;
+};
+
+template <int M, int SG, bool ADJ, bool FIN>
+__device__ __forceinline__ ItemPos item_pos(const PassDesc &d, int T, int gy, int tile) {
+    ItemPos ip;
+    ip.S = gy / d.a_count;
+    ip.a = d.a_lo + gy % d.a_count;
+    ip.p0 = d.p_begin + tile * T;
+    ip.A_off = SG > 0 ? ip.p0 - (1 << (d.k0 + M)) + (1 << d.k0) : ip.p0 + T - 1;
+    ip.D = SG > 0 ? ip.p0 : ip.p0 + T - 1;
+    ip.black = !ADJ && FIN && tile_all_black(d, M, ip.a, ip.p0, T);
+    return ip;
+}
+
+// Block A of a two-block item (MB > 0): warps warp, warp + nwarps, ... load
+// mini-strips of RA source rows, run MA levels in registers and write the
+// results to the shared tile sm (nothing to do for a black tile).
+template <int MA, int MB, int SG, bool ADJ, typename Acc, typename SrcE, typename MidE>
+__device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &G,
+                                             const ItemPos &ip, MidE *sm, int warp, int nwarps,
+                                             int lane) {
+    constexpr int M = MA + MB, RA = 1 << MA, RB = 1 << MB;
+    constexpr int PAD = TilePad<MidE>::kPad;
+    const int P = G.pitch;
+    if (ip.black) return;
+    // mini-strip g (rows g*RA + rho), warp-column wc
+    for (int item = warp; item < RB * G.n_a; item += nwarps) {
+        const int g = item % RB, wc = item / RB;
+        const int i0 = wc * kWarpValid + lane * kV;
+        Acc v[RA][kV];
+        load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, ip.S, ip.a, g * RA, ip.A_off, wc * kWarpValid,
+                                             i0, v);
+        reg_butterfly<MA, Acc>(v);
+        if (lane < kLanesValid) {
+            const int pos = (8 + PAD) * (i0 >> 3);   // i0 is a multiple of 8
+#pragma unroll
+            for (int c = 0; c < RA; ++c) {
+                MidE *row = sm + (g * RA + c) * P + pos;
+                if constexpr (PAD == 2) {
+                    uint32_t *w = reinterpret_cast<uint32_t *>(row);
+#pragma unroll
+                    for (int k = 0; k < kV / 2; ++k)
+                        w[k] = pack_u16x2((uint32_t)v[c][2 * k], (uint32_t)v[c][2 * k + 1]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kV; ++k) row[k] = (MidE)v[c][k];
+                }
+            }
+        }
+    }
+}
+
+// Block B of a two-block item: level-MA slope a2 of every mini-strip g, read
+// from the shared tile with the shear a2*g, MB more levels, then the
+// destination (zeros for a black tile, without reading the tile).
+template <int MA, int MB, int SG, bool ADJ, bool FIN, typename Acc, typename MidE, typename DstE>
+__device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &G,
+                                             const ItemPos &ip, const MidE *sm, int warp,
+                                             int nwarps, int lane) {
+    constexpr int M = MA + MB, RA = 1 << MA, RB = 1 << MB;
+    constexpr int PAD = TilePad<MidE>::kPad;
+    const int P = G.pitch, T = G.tile_out;
+    for (int item = warp; item < RA * G.n_b; item += nwarps) {
+        const int a2 = item % RA, jc = item / RA;
+        const int i0 = jc * kWarpValid + lane * kV;
+        Acc v[RB][kV];
+        if (!ip.black) {
+#pragma unroll
+            for (int g = 0; g < RB; ++g) {
+                const int x0 = i0 + a2 * g;
+                const int delta = x0 & 7;
+                const MidE *row = sm + (g * RA + a2) * P + tile_pos(x0, PAD);
+                MidE raw[kV + PAD];
+#pragma unroll
+                for (int j = 0; j < kV + PAD; ++j) raw[j] = row[j];
+#pragma unroll
+                for (int k = 0; k < kV; ++k)
+                    v[g][k] = (Acc)(k + delta >= kV ? raw[k + PAD] : raw[k]);
+            }
+            reg_butterfly<MB, Acc>(v);
+        } else {
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+#pragma unroll
+                for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
+        }
+        if (lane < kLanesValid && i0 < T) {
+            const DestCols dc = dest_cols<SG, FIN, Acc, DstE>(d, ip.D, i0);
+            if constexpr (ADJ && FIN) {
+                store_image_block<SG, RB, Acc, DstE>(d, hi_row(d, M, ip.S, ip.a, a2 * RB), dc.lo,
+                                                     v);
+            } else {
+                store_rows<SG, FIN, RB, Acc, DstE>(d, dc, hi_row(d, M, ip.S, ip.a, a2 * RB), v);
+            }
+        }
+    }
+}
+
+// One item with all the CTA's warps: single register block (MB = 0), or
+// block A, a CTA barrier, block B.
 // ADJ selects the adjoint form at compile time (cyclic columns, row-mapped
 // gradient source, image-gradient destination) so the forward kernels carry
 // none of its code; FIN likewise selects the final level's destination (the
@@ -676,26 +782,22 @@ __device__ __forceinline__ bool tile_all_black(const PassDesc &d, int M, int a, 
 template <int MA, int MB, int SG, bool ADJ, bool FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm) {
-    constexpr int M = MA + MB, RA = 1 << MA, RB = 1 << MB;
+    constexpr int M = MA + MB, RA = 1 << MA;
     constexpr int PAD = TilePad<MidE>::kPad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const TileGeom G = tile_geom(MA, MB, d.n_a, nwarps, PAD);
     const int T = G.tile_out;
-    const int S = gy / d.a_count, a = d.a_lo + gy % d.a_count;
-    const int p0 = d.p_begin + tile * T;
-    constexpr int sg = SG;
-    const int A_off = sg > 0 ? p0 - (1 << (d.k0 + M)) + (1 << d.k0) : p0 + T - 1;
-    const int D = sg > 0 ? p0 : p0 + T - 1;
-    const bool black = !ADJ && FIN && tile_all_black(d, M, a, p0, T);
+    const ItemPos ip = item_pos<M, SG, ADJ, FIN>(d, T, gy, tile);
 
     if constexpr (MB == 0) {
         // single register block: source -> registers -> destination
         for (int item = warp; item < G.n_a; item += nwarps) {
             const int i0 = item * kWarpValid + lane * kV;
             Acc v[RA][kV];
-            if (!black) {
-                load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, S, a, 0, A_off, item * kWarpValid, i0, v);
+            if (!ip.black) {
+                load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, ip.S, ip.a, 0, ip.A_off,
+                                                     item * kWarpValid, i0, v);
                 reg_butterfly<MA, Acc>(v);
             } else {
 #pragma unroll
@@ -704,78 +806,18 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                     for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
             }
             if (lane < kLanesValid && i0 < T) {
-                const DestCols dc = dest_cols<SG, FIN, Acc, DstE>(d, D, i0);
+                const DestCols dc = dest_cols<SG, FIN, Acc, DstE>(d, ip.D, i0);
                 if constexpr (ADJ && FIN) {
-                    store_image_block<SG, RA, Acc, DstE>(d, hi_row(d, M, S, a, 0), dc.lo, v);
+                    store_image_block<SG, RA, Acc, DstE>(d, hi_row(d, M, ip.S, ip.a, 0), dc.lo, v);
                 } else {
-                    store_rows<SG, FIN, RA, Acc, DstE>(d, dc, hi_row(d, M, S, a, 0), v);
+                    store_rows<SG, FIN, RA, Acc, DstE>(d, dc, hi_row(d, M, ip.S, ip.a, 0), v);
                 }
             }
         }
-        return;
     } else {
-        const int P = G.pitch;
-        if (!black) {
-            // block A: mini-strip g (rows g*RA + rho), warp-column wc
-            for (int item = warp; item < RB * G.n_a; item += nwarps) {
-                const int g = item % RB, wc = item / RB;
-                const int i0 = wc * kWarpValid + lane * kV;
-                Acc v[RA][kV];
-                load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, S, a, g * RA, A_off, wc * kWarpValid, i0, v);
-                reg_butterfly<MA, Acc>(v);
-                if (lane < kLanesValid) {
-                    const int pos = (8 + PAD) * (i0 >> 3);   // i0 is a multiple of 8
-#pragma unroll
-                    for (int c = 0; c < RA; ++c) {
-                        MidE *row = sm + (g * RA + c) * P + pos;
-                        if constexpr (PAD == 2) {
-                            uint32_t *w = reinterpret_cast<uint32_t *>(row);
-#pragma unroll
-                            for (int k = 0; k < kV / 2; ++k)
-                                w[k] = pack_u16x2((uint32_t)v[c][2 * k], (uint32_t)v[c][2 * k + 1]);
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < kV; ++k) row[k] = (MidE)v[c][k];
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        // block B: level-MA slope a2 of every mini-strip g, sheared by a2*g
-        for (int item = warp; item < RA * G.n_b; item += nwarps) {
-            const int a2 = item % RA, jc = item / RA;
-            const int i0 = jc * kWarpValid + lane * kV;
-            Acc v[RB][kV];
-            if (!black) {
-#pragma unroll
-                for (int g = 0; g < RB; ++g) {
-                    const int x0 = i0 + a2 * g;
-                    const int delta = x0 & 7;
-                    const MidE *row = sm + (g * RA + a2) * P + tile_pos(x0, PAD);
-                    MidE raw[kV + PAD];
-#pragma unroll
-                    for (int j = 0; j < kV + PAD; ++j) raw[j] = row[j];
-#pragma unroll
-                    for (int k = 0; k < kV; ++k)
-                        v[g][k] = (Acc)(k + delta >= kV ? raw[k + PAD] : raw[k]);
-                }
-                reg_butterfly<MB, Acc>(v);
-            } else {
-#pragma unroll
-                for (int r = 0; r < RB; ++r)
-#pragma unroll
-                    for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
-            }
-            if (lane < kLanesValid && i0 < T) {
-                const DestCols dc = dest_cols<SG, FIN, Acc, DstE>(d, D, i0);
-                if constexpr (ADJ && FIN) {
-                    store_image_block<SG, RB, Acc, DstE>(d, hi_row(d, M, S, a, a2 * RB), dc.lo, v);
-                } else {
-                    store_rows<SG, FIN, RB, Acc, DstE>(d, dc, hi_row(d, M, S, a, a2 * RB), v);
-                }
-            }
-        }
+        tile_block_a<MA, MB, SG, ADJ, Acc, SrcE, MidE>(d, G, ip, sm, warp, nwarps, lane);
+        if (!ip.black) __syncthreads();   // black is the same for the whole CTA
+        tile_block_b<MA, MB, SG, ADJ, FIN, Acc, MidE, DstE>(d, G, ip, sm, warp, nwarps, lane);
     }
 }
 

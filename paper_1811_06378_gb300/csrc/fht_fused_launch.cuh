@@ -2,11 +2,13 @@
 // fused forward pass (included once per element-type translation unit).
 #pragma once
 
+#include <cstdint>
 #include <cstdio>
 #include <type_traits>
 
 #include "fht_fused.cuh"
 #include "fht_host.h"
+#include "fht_pipe.cuh"
 
 namespace fht {
 
@@ -62,6 +64,57 @@ __global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
 }
 
+namespace {
+// Waits of the pipelined kernels in this translation unit that ran out of
+// their clock budget (read and reset by fht_device_status).
+__device__ unsigned int g_pipe_timeouts = 0;
+
+unsigned int read_reset_pipe_timeouts() {
+    unsigned int v = 0;
+    const unsigned int zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_pipe_timeouts, sizeof v) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_pipe_timeouts, &zero, sizeof zero) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
+
+const bool g_pipe_counter_registered = register_device_counter(&read_reset_pipe_timeouts);
+}  // namespace
+
+template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    fused_pipe_forward_kernel(PassDesc d, int n_items, size_t tile_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[4];
+    pipe_items<MA, MB, SG, false, FIN, Acc, SrcE, MidE, DstE>(d, n_items, tile_bytes, smem_raw,
+                                                              bars, &g_pipe_timeouts);
+}
+
+template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    fused_pipe_adjoint_kernel(PassDesc d, int n_items, size_t tile_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[4];
+    pipe_items<MA, MB, SG, true, FIN, Acc, SrcE, MidE, DstE>(d, n_items, tile_bytes, smem_raw,
+                                                             bars, &g_pipe_timeouts);
+}
+
+template <int MA, int MB, bool ADJ, bool FIN, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
+void (*pipe_kernel_ptr(int sigma))(PassDesc, int, size_t) {
+    if constexpr (ADJ) {
+        return sigma > 0 ? fused_pipe_adjoint_kernel<MA, MB, 1, FIN, Acc, SrcE, MidE, DstE>
+                         : fused_pipe_adjoint_kernel<MA, MB, -1, FIN, Acc, SrcE, MidE, DstE>;
+    } else {
+        return sigma > 0 ? fused_pipe_forward_kernel<MA, MB, 1, FIN, Acc, SrcE, MidE, DstE>
+                         : fused_pipe_forward_kernel<MA, MB, -1, FIN, Acc, SrcE, MidE, DstE>;
+    }
+}
+
 // Which final-level flags a type combination can take: uint16 is only ever an
 // intermediate level, and a uint8 image goes to int32 only in a single
 // (final) pass.
@@ -84,8 +137,63 @@ void (*fused_kernel_ptr(int sigma))(PassDesc) {
     }
 }
 
+// Persistent pipelined launch of a two-block pass (MB > 0): one CTA of two
+// warp groups per SM, two shared tiles. Returns cudaErrorNotSupported when
+// two tiles do not fit one block's shared memory (the caller then uses the
+// one-item-per-CTA kernel).
+template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
+cudaError_t launch_pipe_t(PassDesc d, cudaStream_t st) {
+    constexpr int PAD = TilePad<MidE>::kPad;
+    TileGeom G = tile_geom(MA, MB, d.n_a, kPipeGroupWarps, PAD);
+    size_t tile_bytes = pipe_tile_bytes(G, MA, MB, sizeof(MidE));
+    while (2 * tile_bytes > kMaxTileSmem && d.n_a > 1) {
+        d.n_a--;
+        G = tile_geom(MA, MB, d.n_a, kPipeGroupWarps, PAD);
+        tile_bytes = pipe_tile_bytes(G, MA, MB, sizeof(MidE));
+    }
+    if (2 * tile_bytes > kMaxTileSmem) return cudaErrorNotSupported;
+    const size_t smem = 2 * tile_bytes;
+    d.tile_w = G.tile_out;
+    d.tiles = (d.p_count + G.tile_out - 1) / G.tile_out;
+    const long long items = (long long)d.tiles * d.s_count * d.a_count;
+    if (items == 0) return cudaSuccess;
+    if (items > INT32_MAX) return cudaErrorInvalidValue;
+    using FC = FinCases<ADJ, SrcE, DstE>;
+    void (*k)(PassDesc, int, size_t) = nullptr;
+    if (d.hi_final) {
+        if constexpr (FC::kFinal) k = pipe_kernel_ptr<MA, MB, ADJ, true, Acc, SrcE, MidE, DstE>(d.sigma);
+    } else {
+        if constexpr (FC::kLevel) k = pipe_kernel_ptr<MA, MB, ADJ, false, Acc, SrcE, MidE, DstE>(d.sigma);
+    }
+    if (!k) return cudaErrorInvalidValue;   // a type combination no plan produces
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPipeThreads, smem)) !=
+        cudaSuccess)
+        return e;
+    const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(items < slots ? items : slots);
+    char name[64];
+    snprintf(name, sizeof name, "%s_m%d_%s%s", ADJ ? "adjoint_fused" : "forward_fused",
+             MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "");
+    LaunchScope scope(name, st, pass_alg_bytes(d, MA + MB, sizeof(SrcE), sizeof(DstE)));
+    k<<<grid, kPipeThreads, smem, st>>>(d, (int)items, tile_bytes);
+    scope.done();
+    return cudaGetLastError();
+}
+
 template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
 cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
+    if constexpr (MB > 0) {
+        if (pipe_enabled()) {
+            const cudaError_t e = launch_pipe_t<MA, MB, ADJ, Acc, SrcE, MidE, DstE>(d, st);
+            if (e != cudaErrorNotSupported) return e;
+        }
+    }
     TileGeom G = tile_geom(MA, MB, d.n_a, kFusedWarps, TilePad<MidE>::kPad);
     size_t smem = MB == 0 ? 0 : (size_t)(1 << (MA + MB)) * G.pitch * sizeof(MidE);
     // A tuned tile width that does not fit one block's shared memory is

@@ -324,3 +324,9 @@ def test_config_batch_shapes_per_image(fht):
     imgs = edge_batch(shapes, seed=3)
     for img in imgs:
         assert (host(fht.forward(dev(img), 0)) == O.quadrant(img, 0)).all()
+
+
+def test_zz_no_pipelined_wait_timed_out(fht):
+    """Every pipelined pass run by this module finished all its hand-offs
+    (runs last in the module: the count covers all the launches above)."""
+    assert fht.device_status() == fht.FHT_OK

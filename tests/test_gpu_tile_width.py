@@ -1,12 +1,15 @@
-"""Tile width of the fused passes: any FHT_TUNE setting gives the same result.
+"""Tile width and kernel form of the fused passes: any FHT_TUNE setting, with
+one item per CTA (default) or the persistent pipelined kernel (FHT_PIPE=1),
+gives the same result.
 
 FHT_TUNE="a,b" sets how many warp-widths of source columns one tile's first
 block of levels covers (a: first passes over uint8 images, whose shared tile
 holds uint16; b: tiles of 4-byte values). Wider tiles re-read less of the
 halo but need more shared memory; a width whose tile does not fit one block's
 shared memory is narrowed at launch. The setting is read when the library
-loads, so each width runs in a child process and its result is compared bit
-for bit with the oracle."""
+loads, so each setting runs in a child process and its result is compared
+bit for bit with the oracle. The child also checks that no pipelined wait ran
+out of its budget."""
 
 import os
 import subprocess
@@ -30,16 +33,18 @@ f = random_image(700, 900, "f32", seed=22)
 out = [fht.forward(torch.from_numpy(img).cuda(), q).cpu().numpy() for q in range(4)]
 out += [fht.forward(torch.from_numpy(f).cuda(), q, acc=torch.float32).cpu().numpy()
         for q in (0, 2)]
+assert fht.device_status() == fht.FHT_OK
 np.savez(sys.argv[1], *out)
 """
 
 
-@pytest.mark.parametrize("tune", ["1,1", "3,3", "2,2"])
-def test_tile_width_setting_is_bit_exact(tune, tmp_path):
+@pytest.mark.parametrize("tune,pipe", [("1,1", "0"), ("3,3", "0"), ("2,2", "0"), ("1,1", "1"),
+                                       ("3,3", "1"), ("2,2", "1")])
+def test_tile_width_setting_is_bit_exact(tune, pipe, tmp_path):
     import oracle as O
     from workloads import edges_and_lines, random_image
     path = str(tmp_path / "out.npz")
-    env = dict(os.environ, FHT_TUNE=tune, PYTHONPATH=ROOT)
+    env = dict(os.environ, FHT_TUNE=tune, FHT_PIPE=pipe, PYTHONPATH=ROOT)
     r = subprocess.run([sys.executable, "-c", CHILD, path], env=env, cwd=ROOT,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
