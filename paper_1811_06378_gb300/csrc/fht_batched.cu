@@ -28,11 +28,15 @@ struct fht_plan {
     int f32 = 0;
     int sigma = 1;
     int n_segs = 0, total_items = 0;
-    size_t table_bytes = 0, descs_off = 0, counters_off = 0, done_off = 0, levels_off = 0;
+    size_t table_bytes = 0, counters_off = 0, done_off = 0, levels_off = 0;
     size_t ws_bytes = 0, smem = 0;
     int n_done = 0;
     std::vector<int> h, w, rows, cols;   // per image: size, and its quadrant's n x W
-    void *host_table = nullptr;   // pinned staging: segment table, then image descriptors
+    // pinned staging of the segment table: [0, counters_off) for direct
+    // launches, [counters_off, 2 counters_off) for the latest stream capture
+    void *host_table = nullptr;
+    cudaEvent_t copied = nullptr;   // after the last direct launch's table copy
+    bool copy_pending = false;
     long long wait_budget = 4000000000LL;   // ~2 s of SM clocks
     int dep_bias = 0;
 };
@@ -172,8 +176,7 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
     P->n_done = n_done;
     P->smem = smem;
     P->table_bytes = segs.size() * sizeof(BatchSeg);
-    P->descs_off = align256(P->table_bytes);
-    P->counters_off = align256(P->descs_off + (size_t)count * sizeof(fht_image_desc));
+    P->counters_off = align256(P->table_bytes);
     P->done_off = P->counters_off + 256;
     P->levels_off = align256(P->done_off + (size_t)n_done * sizeof(unsigned int));
     // intermediate offsets inside the workspace
@@ -190,12 +193,20 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
         P->rows.push_back(r);
         P->cols.push_back(c);
     }
-    if (cudaMallocHost(&P->host_table, P->counters_off) != cudaSuccess) {
+    if (cudaMallocHost(&P->host_table, 2 * P->counters_off) != cudaSuccess) {
         cudaGetLastError();
         delete P;
         return FHT_ENOMEM;
     }
-    std::memcpy(P->host_table, segs.data(), P->table_bytes);
+    if (cudaEventCreateWithFlags(&P->copied, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(P->host_table);
+        delete P;
+        return FHT_ECUDA;
+    }
+    for (int c = 0; c < 2; ++c)
+        std::memcpy(static_cast<unsigned char *>(P->host_table) + c * P->counters_off,
+                    segs.data(), P->table_bytes);
     *plan = P;
     *workspace_bytes = P->ws_bytes;
     return FHT_OK;
@@ -212,10 +223,39 @@ fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void
     }
     cudaStream_t st = (cudaStream_t)stream;
     unsigned char *ws = static_cast<unsigned char *>(workspace);
-    std::memcpy(static_cast<unsigned char *>(plan->host_table) + plan->descs_off, descs,
-                (size_t)plan->count * sizeof(fht_image_desc));
-    cudaError_t e = cudaMemcpyAsync(ws, plan->host_table, plan->counters_off,
-                                    cudaMemcpyHostToDevice, st);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FHT_ECUDA;
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    // the previous direct launch's copy must have read the table before it
+    // is rewritten
+    if (!capturing && plan->copy_pending) {
+        if (cudaEventSynchronize(plan->copied) != cudaSuccess) return FHT_ECUDA;
+        plan->copy_pending = false;
+    }
+    unsigned char *table =
+        static_cast<unsigned char *>(plan->host_table) + (capturing ? plan->counters_off : 0);
+    BatchSeg *segs = reinterpret_cast<BatchSeg *>(table);
+    for (int i = 0; i < plan->n_segs; ++i) {
+        BatchSeg &sg = segs[i];
+        const fht_image_desc &im = descs[sg.image];
+        if (sg.lo_from_image) {
+            sg.d.lo.ptr = const_cast<void *>(im.img);
+            sg.d.lo.pitch = im.img_pitch;
+        } else {
+            sg.d.lo.ptr = ws + sg.lo_off;
+        }
+        if (sg.hi_from_image) {
+            sg.d.hi.ptr = im.out;
+            sg.d.hi.pitch = im.out_pitch;
+        } else {
+            sg.d.hi.ptr = ws + sg.hi_off;
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(ws, table, plan->counters_off, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !capturing) {
+        e = cudaEventRecord(plan->copied, st);
+        if (e == cudaSuccess) plan->copy_pending = true;
+    }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ws + plan->counters_off, 0,
                             plan->levels_off - plan->counters_off, st);
@@ -235,7 +275,6 @@ fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void
     LaunchScope scope(plan->f32 ? "batched_forward_f32" : "batched_forward_u8_i32", st, 0.0);
     k<<<grid, kWarps * 32, plan->smem, st>>>(
         reinterpret_cast<const BatchSeg *>(ws), plan->n_segs, plan->total_items,
-        reinterpret_cast<const fht_image_desc *>(ws + plan->descs_off), ws,
         reinterpret_cast<Counters *>(ws + plan->counters_off),
         reinterpret_cast<unsigned int *>(ws + plan->done_off), plan->wait_budget,
         plan->dep_bias);
@@ -265,6 +304,10 @@ fht_status fht_batched_test_hooks(fht_plan *plan, long long wait_budget_cycles, 
 
 void fht_plan_destroy(fht_plan *plan) {
     if (!plan) return;
+    if (plan->copied) {
+        if (plan->copy_pending) cudaEventSynchronize(plan->copied);
+        cudaEventDestroy(plan->copied);
+    }
     if (plan->host_table) cudaFreeHost(plan->host_table);
     delete plan;
 }

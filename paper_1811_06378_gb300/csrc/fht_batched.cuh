@@ -21,7 +21,7 @@ constexpr int kMaxSegsShared = 2048;   // segment keys kept in shared memory
 enum : int { kVarU8Final = 0, kVarU8Level = 10, kVarU16Final = 20, kVarF32 = 30 };
 
 struct BatchSeg {
-    PassDesc d;          // lo/hi filled on the device from the image table / workspace
+    PassDesc d;          // complete; lo/hi pointers and pitches written by the host per call
     int image, variant, m;
     int item_begin, tiles;
     int done_index;      // counter of this (image, pass)
@@ -65,107 +65,116 @@ __device__ __forceinline__ void run_item_m(int m, const PassDesc &d, int gy, int
     }
 }
 
-// one batch = one quadrant, so one sign: the kernel is instantiated per sign
+// one batch = one quadrant, so one sign: the kernel is instantiated per sign.
+// Thread 0 claims the next item while the CTA works on the current one (the
+// claim's latency is hidden), finds its segment and waits for its dependency;
+// all threads then copy the segment's pass descriptor (complete, pointers
+// included, written by the host) into shared memory. After an item thread 0
+// alone fences and counts it done: the CTA barrier before it orders every
+// thread's stores before that release.
+// Holding one claimed item ahead keeps the waits finite: the smallest
+// unfinished item is always some CTA's current item, and everything it
+// depends on has a smaller index.
 template <bool F32, int SG>
 __global__ void __launch_bounds__(kWarps * 32, 2)
-    batched_forward_kernel(const BatchSeg *segs, int n_segs, int total_items,
-                           const fht_image_desc *descs, unsigned char *ws, Counters *ctr,
+    batched_forward_kernel(const BatchSeg *segs, int n_segs, int total_items, Counters *ctr,
                            unsigned int *done, long long wait_budget, int dep_bias) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_item, s_seg, s_skip;
-    __shared__ PassDesc s_desc;   // the current item's pass, pointers patched
+    __shared__ int s_item, s_skip, s_m, s_variant, s_tiles, s_first, s_done;
+    __shared__ int s_seg;
+    __shared__ PassDesc s_desc;   // the current item's pass
     __shared__ int s_begin[kMaxSegsShared];   // segment start items, for the search
     const bool keys_shared = n_segs <= kMaxSegsShared;
     if (keys_shared)
         for (int i = threadIdx.x; i < n_segs; i += blockDim.x) s_begin[i] = segs[i].item_begin;
+    int next = 0;   // thread 0: the claimed next item
+    if (threadIdx.x == 0) next = (int)atomicAdd(&ctr->next_item, 1u);
+    __syncthreads();   // s_begin complete
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(&ctr->next_item, 1u);
+        if (threadIdx.x == 0) {
+            const int item = next;
+            s_item = item;
+            if (item < total_items) {
+                next = (int)atomicAdd(&ctr->next_item, 1u);
+                // the segment holding this item (segments are sorted by item_begin)
+                int lo = 0, hi = n_segs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    const int b = keys_shared ? s_begin[mid] : segs[mid].item_begin;
+                    if (b <= item) lo = mid;
+                    else hi = mid - 1;
+                }
+                const BatchSeg &sg = segs[lo];
+                s_seg = lo;
+                s_m = sg.m;
+                s_variant = sg.variant;
+                s_tiles = sg.tiles;
+                s_first = sg.item_begin;
+                s_done = sg.done_index;
+                int skip = 0;
+                if (sg.dep_index >= 0) {
+                    const unsigned int need = (unsigned int)(sg.dep_count + dep_bias);
+                    const long long t0 = clock64();
+                    while (ld_acquire(done + sg.dep_index) < need) {
+                        __nanosleep(256);
+                        if (clock64() - t0 > wait_budget) {
+                            atomicExch(&ctr->error, (int)FHT_ETIMEOUT);
+                            skip = 1;
+                            break;
+                        }
+                    }
+                }
+                s_skip = skip;
+            }
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= total_items) break;
-        if (threadIdx.x == 0) {
-            // the segment holding this item (segments are sorted by item_begin)
-            int lo = 0, hi = n_segs - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                const int b = keys_shared ? s_begin[mid] : segs[mid].item_begin;
-                if (b <= item) lo = mid;
-                else hi = mid - 1;
-            }
-            s_seg = lo;
-            int skip = 0;
-            const BatchSeg &sg = segs[lo];
-            if (sg.dep_index >= 0) {
-                const unsigned int need = (unsigned int)(sg.dep_count + dep_bias);
-                const long long t0 = clock64();
-                while (ld_acquire(done + sg.dep_index) < need) {
-                    __nanosleep(256);
-                    if (clock64() - t0 > wait_budget) {
-                        atomicExch(&ctr->error, (int)FHT_ETIMEOUT);
-                        skip = 1;
-                        break;
-                    }
-                }
-            }
-            s_skip = skip;
-        }
-        __syncthreads();
         {
-            // all threads copy the pass descriptor, then one patches its pointers
             const int *src = reinterpret_cast<const int *>(&segs[s_seg].d);
             int *dst = reinterpret_cast<int *>(&s_desc);
             for (int i = threadIdx.x; i < (int)(sizeof(PassDesc) / sizeof(int)); i += blockDim.x)
                 dst[i] = src[i];
         }
         __syncthreads();
-        if (threadIdx.x == 0 && !s_skip) {
-            const BatchSeg &sg = segs[s_seg];
-            const fht_image_desc &im = descs[sg.image];
-            s_desc.lo.ptr = sg.lo_from_image ? const_cast<void *>(im.img) : (void *)(ws + sg.lo_off);
-            if (sg.lo_from_image) s_desc.lo.pitch = im.img_pitch;
-            s_desc.hi.ptr = sg.hi_from_image ? im.out : (void *)(ws + sg.hi_off);
-            if (sg.hi_from_image) s_desc.hi.pitch = im.out_pitch;
-        }
-        __syncthreads();
-        const BatchSeg &sg = segs[s_seg];
-        if (!s_skip) {
+        const bool skip = s_skip != 0;
+        if (!skip) {
             const PassDesc &d = s_desc;
-            const int local = item - sg.item_begin;
-            const int gy = local / sg.tiles, tile = local - gy * sg.tiles;
+            const int local = item - s_first, m = s_m;
+            const int gy = local / s_tiles, tile = local - gy * s_tiles;
             if constexpr (F32) {
                 if (d.hi_final)
-                    run_item_m<SG, true, float, float, float, float>(sg.m, d, gy, tile, smem_raw);
+                    run_item_m<SG, true, float, float, float, float>(m, d, gy, tile, smem_raw);
                 else
-                    run_item_m<SG, false, float, float, float, float>(sg.m, d, gy, tile, smem_raw);
+                    run_item_m<SG, false, float, float, float, float>(m, d, gy, tile, smem_raw);
             } else {
                 // a uint8 image is finished in one pass or goes to a uint16
                 // level; a uint16 level's pass is the last (two passes at most)
-                switch (sg.variant) {
+                switch (s_variant) {
                 case kVarU8Final:
-                    run_item_m<SG, true, int32_t, uint8_t, uint16_t, int32_t>(sg.m, d, gy, tile,
+                    run_item_m<SG, true, int32_t, uint8_t, uint16_t, int32_t>(m, d, gy, tile,
                                                                              smem_raw);
                     break;
                 case kVarU8Level:
-                    run_item_m<SG, false, int32_t, uint8_t, uint16_t, uint16_t>(sg.m, d, gy, tile,
+                    run_item_m<SG, false, int32_t, uint8_t, uint16_t, uint16_t>(m, d, gy, tile,
                                                                                smem_raw);
                     break;
                 default:
-                    run_item_m<SG, true, int32_t, uint16_t, int32_t, int32_t>(sg.m, d, gy, tile,
+                    run_item_m<SG, true, int32_t, uint16_t, int32_t, int32_t>(m, d, gy, tile,
                                                                              smem_raw);
                     break;
                 }
             }
         }
-        // make this item's stores visible GPU-wide before announcing it
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0 && !s_skip) atomicAdd(done + sg.done_index, 1u);
+        __syncthreads();   // every thread's stores of this item precede the release below
+        if (threadIdx.x == 0 && !skip) {
+            __threadfence();
+            atomicAdd(done + s_done, 1u);
+        }
     }
 }
 
-
-using Kernel = void (*)(const BatchSeg *, int, int, const fht_image_desc *, unsigned char *,
-                        Counters *, unsigned int *, long long, int);
+using Kernel = void (*)(const BatchSeg *, int, int, Counters *, unsigned int *, long long, int);
 
 // The four instantiations, one per translation unit.
 Kernel kernel_f32_pos();

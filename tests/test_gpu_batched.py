@@ -86,3 +86,52 @@ def test_batched_wait_timeout_is_reported(fht):
     assert plan.status() == 0
     for x, o in zip(imgs, outs):
         assert torch.equal(o, fht.forward(x, 0))
+
+
+def test_batched_back_to_back_calls_keep_their_descriptors(fht):
+    """Two direct calls on one plan and stream, different images and outputs,
+    no synchronisation between them: each launch uses its own call's
+    descriptors (the plan's staging table is not rewritten before the first
+    call's copy of it has run)."""
+    shapes = [(300, 200), (64, 700), (513, 90)]
+    a = [torch.from_numpy(x).cuda() for x in edge_batch(shapes, seed=21)]
+    b = [torch.from_numpy(x).cuda() for x in edge_batch(shapes, seed=22)]
+    plan = fht.BatchPlan(shapes, 1)
+    ws = plan.workspace("cuda")
+    torch.cuda._sleep(50_000_000)   # keep the stream busy so the copies are still queued
+    oa = plan.forward(a, workspace=ws)
+    ob = plan.forward(b, workspace=ws)
+    torch.cuda.synchronize()
+    assert plan.status(ws) == 0
+    for x, o in zip(a, oa):
+        assert torch.equal(o, fht.forward(x, 1))
+    for x, o in zip(b, ob):
+        assert torch.equal(o, fht.forward(x, 1))
+
+
+def test_batched_graph_keeps_captured_descriptors(fht):
+    """A direct call after a capture does not change what the graph replays."""
+    shapes = [(200, 300), (129, 64)]
+    a = [torch.from_numpy(x).cuda() for x in edge_batch(shapes, seed=31)]
+    b = [torch.from_numpy(x).cuda() for x in edge_batch(shapes, seed=32)]
+    plan = fht.BatchPlan(shapes, 0)
+    ws_g = plan.workspace("cuda")
+    ws_d = plan.workspace("cuda")
+    oa = [torch.empty(fht.query_shape(h, w, 0), dtype=torch.int32, device="cuda")
+          for h, w in shapes]
+    plan.forward(a, oa, ws_g)   # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.forward(a, oa, ws_g, stream=s)
+    ob = plan.forward(b, workspace=ws_d)
+    for o in oa:
+        o.fill_(-1)
+    g.replay()
+    torch.cuda.synchronize()
+    for x, o in zip(a, oa):
+        assert torch.equal(o, fht.forward(x, 0))
+    for x, o in zip(b, ob):
+        assert torch.equal(o, fht.forward(x, 0))
