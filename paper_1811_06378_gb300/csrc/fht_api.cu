@@ -295,6 +295,9 @@ PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &fina
     int drop = P.K - P.k[p];
     d.a_lo = t_lo >> drop;
     d.a_count = (t_hi >> drop) - d.a_lo + 1;
+    const int drop1 = P.K - P.k[p + 1];
+    d.need_lo = t_lo >> drop1;
+    d.need_hi = t_hi >> drop1;
     d.s_count = P.n >> P.k[p + 1];
     d.p_begin = 0;
     d.p_count = d.hi.cols;

@@ -110,6 +110,8 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
             d.sigma = sigma;
             d.a_lo = 0;
             d.a_count = 1 << k0;
+            d.need_lo = 0;
+            d.need_hi = (1 << k1) - 1;
             d.s_count = n >> k1;
             d.t_first = 0;
             d.t_last = n - 1;

@@ -58,6 +58,9 @@ struct PassDesc {
     int dst_image, dst_h, dst_w, dst_transpose, accumulate;
     int p_begin, p_count;  // destination columns [p_begin, p_begin + p_count) are tiled
     int a_lo, a_count;   // level-k0 slopes of the groups (range pruning)
+    // level-k1 slopes [need_lo, need_hi] that later passes or the output use;
+    // an item producing none of them is skipped (range pruning inside groups)
+    int need_lo, need_hi;
     int s_count;         // strips at level k1
     int tile_w;          // output columns per tile
     int tiles;           // tiles per group

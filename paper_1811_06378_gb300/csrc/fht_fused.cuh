@@ -738,6 +738,10 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
     const int P = G.pitch, T = G.tile_out;
     for (int item = warp; item < RA * G.n_b; item += nwarps) {
         const int a2 = item % RA, jc = item / RA;
+        // level-k1 slopes (a << M) + a2*RB .. + RB - 1 of this item: skip it
+        // when none is used later
+        const int slope0 = (ip.a << M) + a2 * RB;
+        if (slope0 > d.need_hi || slope0 + RB - 1 < d.need_lo) continue;
         const int i0 = jc * kWarpValid + lane * kV;
         Acc v[RB][kV];
         if (!ip.black) {

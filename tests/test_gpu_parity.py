@@ -326,6 +326,23 @@ def test_config_batch_shapes_per_image(fht):
         assert (host(fht.forward(dev(img), 0)) == O.quadrant(img, 0)).all()
 
 
+@pytest.mark.parametrize("h,w,q", [(2048, 300, 0), (1500, 2000, 2), (8192, 700, 1), (700, 8192, 3)])
+def test_range_pruning_matches_full_rows(fht, h, w, q):
+    """forward_range skips butterfly items whose slopes no later pass uses;
+    ranges that start and end inside items, groups and passes (two-pass
+    K = 11, three-pass K = 13) give exactly the rows of the full quadrant,
+    itself checked against the oracle by the other tests."""
+    x = dev(edges_and_lines(h, w, seed=h + w + q))
+    full = fht.forward(x, q)
+    n = full.shape[0]
+    rng = np.random.default_rng(q)
+    cases = [(0, 0), (n - 1, n - 1), (5, 9), (63, 64), (100, 131), (n // 2 - 3, n // 2 + 70)]
+    cases += [tuple(sorted(rng.integers(0, n, size=2))) for _ in range(4)]
+    for t_lo, t_hi in cases:
+        got = fht.forward_range(x, q, int(t_lo), int(t_hi))
+        assert torch.equal(got, full[t_lo:t_hi + 1]), (t_lo, t_hi)
+
+
 def test_zz_no_pipelined_wait_timed_out(fht):
     """Every pipelined pass run by this module finished all its hand-offs
     (runs last in the module: the count covers all the launches above)."""
