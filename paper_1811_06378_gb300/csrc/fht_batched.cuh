@@ -44,14 +44,14 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     return v;
 }
 
-template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __device__ __forceinline__ void run_item(const PassDesc &d, int gy, int tile, unsigned char *sm) {
     fused_forward_item<MA, MB, SG, false, FIN, Acc, SrcE, MidE, DstE>(
         d, gy, tile, reinterpret_cast<MidE *>(sm));
 }
 
-template <int SG, bool FIN, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int SG, int FIN, typename Acc, typename SrcE, typename MidE, typename DstE>
 __device__ __forceinline__ void run_item_m(int m, const PassDesc &d, int gy, int tile,
                                            unsigned char *sm) {
     switch (m) {
@@ -144,23 +144,23 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
             const int gy = local / s_tiles, tile = local - gy * s_tiles;
             if constexpr (F32) {
                 if (d.hi_final)
-                    run_item_m<SG, true, float, float, float, float>(m, d, gy, tile, smem_raw);
+                    run_item_m<SG, 1, float, float, float, float>(m, d, gy, tile, smem_raw);
                 else
-                    run_item_m<SG, false, float, float, float, float>(m, d, gy, tile, smem_raw);
+                    run_item_m<SG, 0, float, float, float, float>(m, d, gy, tile, smem_raw);
             } else {
                 // a uint8 image is finished in one pass or goes to a uint16
                 // level; a uint16 level's pass is the last (two passes at most)
                 switch (s_variant) {
                 case kVarU8Final:
-                    run_item_m<SG, true, int32_t, uint8_t, uint16_t, int32_t>(m, d, gy, tile,
+                    run_item_m<SG, 1, int32_t, uint8_t, uint16_t, int32_t>(m, d, gy, tile,
                                                                              smem_raw);
                     break;
                 case kVarU8Level:
-                    run_item_m<SG, false, int32_t, uint8_t, uint16_t, uint16_t>(m, d, gy, tile,
+                    run_item_m<SG, 0, int32_t, uint8_t, uint16_t, uint16_t>(m, d, gy, tile,
                                                                                smem_raw);
                     break;
                 default:
-                    run_item_m<SG, true, int32_t, uint16_t, int32_t, int32_t>(m, d, gy, tile,
+                    run_item_m<SG, 1, int32_t, uint16_t, int32_t, int32_t>(m, d, gy, tile,
                                                                              smem_raw);
                     break;
                 }

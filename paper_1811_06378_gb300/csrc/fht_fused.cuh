@@ -476,7 +476,7 @@ struct DestCols {
     bool vec;     // the 8 land contiguously, in bounds and 16-byte aligned
 };
 
-template <int SG, bool FIN, typename Acc, typename DstE>
+template <int SG, int FIN, typename Acc, typename DstE>
 __device__ __forceinline__ DestCols dest_cols(const PassDesc &d, int D, int i0) {
     DestCols c;
     constexpr int sg = SG;
@@ -525,7 +525,7 @@ __device__ __noinline__ void store_final_edge(const PassDesc &d, DstE *row, int 
 // Store R consecutive level-k1 rows hi_r0.. of this lane's 8 columns: one base
 // pointer plus a stride per row; for the final level the rows outside
 // [t_first, t_last] (range / full-image maps) are skipped.
-template <int SG, bool FIN, int R, typename Acc, typename DstE>
+template <int SG, int FIN, int R, typename Acc, typename DstE>
 __device__ __forceinline__ void store_rows(const PassDesc &d, const DestCols &c, int hi_r0,
                                            const Acc (&v)[R][kV]) {
     DstE *base = reinterpret_cast<DstE *>(d.hi.ptr);
@@ -573,82 +573,184 @@ __device__ __forceinline__ E acc_store(E old, Acc v, bool acc) {
     return acc ? (E)Arith<Acc>::add((Acc)old, v) : (E)v;
 }
 
-template <int SG, int R, typename Acc, typename DstE>
+// Out-of-line fallbacks of store_image_block (crop edges, unaligned rows).
+// One image row: the lane's 8 ascending columns p = lo.. at X0.., those with
+// p in [p_lo, p_hi) only.
+template <typename Acc, typename DstE>
+__device__ __noinline__ void store_image_row_edge(DstE *row, int X0, int lo, int p_lo, int p_hi,
+                                                  int acc, Vec8<Acc> a) {
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        const int p = lo + k;
+        if (p >= p_lo && p < p_hi) row[X0 + k] = acc_store<DstE, Acc>(row[X0 + k], a.x[k], acc);
+    }
+}
+
+// One image row X of a transposed destination: columns y0..y0+R-1 (< dst_h).
+template <int R, typename Acc, typename DstE>
+__device__ __noinline__ void store_image_col_edge(DstE *row, int y0, int dst_h, int acc,
+                                                  Vec8<Acc> col) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = y0 + r;
+        if (y < dst_h) row[y] = acc_store<DstE, Acc>(row[y], col.x[r], acc);
+    }
+}
+
+// Final level of an adjoint: R consecutive output rows y0.. x this lane's 8
+// columns go to the image gradient, cropped to dst_h x dst_w, transposed for
+// the horizontal quadrants (TR), added to the gradient already there when
+// accumulating. Columns p in [p_begin, p_begin + p_count) are exactly the
+// image columns X = p - sigma_plus*n < dst_w (a tile wider than W would
+// otherwise reach the same X again through the cyclic wrap). When
+// accumulating, the old values of up to 4 rows (columns) are loaded before
+// any of their sums is stored, so those loads are in flight together.
+template <int SG, bool TR, int R, typename Acc, typename DstE>
 __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int lo,
                                                   const Acc (&v)[R][kV]) {
-    // columns p in [p_begin, p_begin + p_count) are exactly the image columns
-    // X = p - sigma_plus*n < dst_w; a tile wider than W would otherwise reach
-    // the same X again through the cyclic wrap
     constexpr int sg = SG;
-    const bool acc = d.accumulate != 0;
+    constexpr int kB = 4;   // rows (columns) whose old values are loaded together
+    const int acc = d.accumulate;
     const int p_lo = d.p_begin, p_hi = d.p_begin + d.p_count;
     const int X0 = lo - (sg > 0 ? d.n : 0);   // column of p = lo (valid when lo >= p_lo)
     DstE *img = reinterpret_cast<DstE *>(d.hi.ptr);
     const int64_t pitch = d.hi.pitch;
     const bool inside = lo >= p_lo && lo + kV <= p_hi;
-    if (!d.dst_transpose) {
+    using V4 = typename std::conditional<std::is_same<DstE, float>::value, float4, int4>::type;
+    if constexpr (!TR) {
         const bool vec = inside && (X0 & 3) == 0 && (pitch & 3) == 0 &&
                          ((reinterpret_cast<uintptr_t>(img) & 15) == 0);
+        const int rows = d.dst_h - y0;   // rows r < rows exist
+        if (vec) {
+            DstE *base = img + (int64_t)y0 * pitch + X0;
+            if (!acc) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int y = y0 + r;
-            if (y >= d.dst_h) continue;
-            DstE *row = img + (int64_t)y * pitch;
-            Acc asc[kV];
-#pragma unroll
-            for (int k = 0; k < kV; ++k) asc[k] = sg > 0 ? v[r][k] : v[r][kV - 1 - k];
-            if (vec) {
-                if (acc) {
-                    Acc old[kV];
-                    load8<DstE, Acc>(row, X0, X0 + kV, old);
-#pragma unroll
-                    for (int k = 0; k < kV; ++k) asc[k] = Arith<Acc>::add(old[k], asc[k]);
+                for (int r = 0; r < R; ++r) {
+                    if (r >= rows) continue;
+                    V4 a, b;
+                    a.x = (DstE)v[r][sg > 0 ? 0 : 7];
+                    a.y = (DstE)v[r][sg > 0 ? 1 : 6];
+                    a.z = (DstE)v[r][sg > 0 ? 2 : 5];
+                    a.w = (DstE)v[r][sg > 0 ? 3 : 4];
+                    b.x = (DstE)v[r][sg > 0 ? 4 : 3];
+                    b.y = (DstE)v[r][sg > 0 ? 5 : 2];
+                    b.z = (DstE)v[r][sg > 0 ? 6 : 1];
+                    b.w = (DstE)v[r][sg > 0 ? 7 : 0];
+                    V4 *q = reinterpret_cast<V4 *>(base + r * pitch);
+                    q[0] = a;
+                    q[1] = b;
                 }
-                store8<DstE, Acc>(row, X0, X0 + kV, asc);
-            } else {
+                return;
+            }
+#pragma unroll
+            for (int r0 = 0; r0 < R; r0 += kB) {
+                constexpr int B = R < kB ? R : kB;
+                V4 old[B][2];
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    if (r0 + j < rows) {
+                        const V4 *q = reinterpret_cast<const V4 *>(base + (r0 + j) * pitch);
+                        old[j][0] = q[0];
+                        old[j][1] = q[1];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    const int r = r0 + j;
+                    if (r >= rows) continue;
+                    Acc asc[kV];
+#pragma unroll
+                    for (int k = 0; k < kV; ++k) asc[k] = sg > 0 ? v[r][k] : v[r][kV - 1 - k];
+                    V4 a, b;
+                    a.x = (DstE)Arith<Acc>::add((Acc)old[j][0].x, asc[0]);
+                    a.y = (DstE)Arith<Acc>::add((Acc)old[j][0].y, asc[1]);
+                    a.z = (DstE)Arith<Acc>::add((Acc)old[j][0].z, asc[2]);
+                    a.w = (DstE)Arith<Acc>::add((Acc)old[j][0].w, asc[3]);
+                    b.x = (DstE)Arith<Acc>::add((Acc)old[j][1].x, asc[4]);
+                    b.y = (DstE)Arith<Acc>::add((Acc)old[j][1].y, asc[5]);
+                    b.z = (DstE)Arith<Acc>::add((Acc)old[j][1].z, asc[6]);
+                    b.w = (DstE)Arith<Acc>::add((Acc)old[j][1].w, asc[7]);
+                    V4 *q = reinterpret_cast<V4 *>(base + r * pitch);
+                    q[0] = a;
+                    q[1] = b;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r >= rows) continue;
+                Vec8<Acc> a;
+#pragma unroll
+                for (int k = 0; k < kV; ++k) a.x[k] = sg > 0 ? v[r][k] : v[r][kV - 1 - k];
+                store_image_row_edge<Acc, DstE>(img + (int64_t)(y0 + r) * pitch, X0, lo, p_lo,
+                                                p_hi, acc, a);
+            }
+        }
+    } else {
+        // transposed: column k of the lane's 8 is image row X0 + k, image
+        // columns y0 .. y0 + R - 1
+        bool vec = false;
+        if constexpr (R >= 4) {
+            vec = inside && y0 + R <= d.dst_h && (pitch & 3) == 0 &&
+                  ((reinterpret_cast<uintptr_t>(img + y0) & 15) == 0);
+        }
+        if (vec) {
+            constexpr int NV = R / 4 > 0 ? R / 4 : 1;   // 16-byte vectors per column
+            if (!acc) {
 #pragma unroll
                 for (int k = 0; k < kV; ++k) {
-                    const int p = lo + k;
-                    if (p >= p_lo && p < p_hi)
-                        row[X0 + k] = acc_store<DstE, Acc>(row[X0 + k], asc[k], acc);
+                    const int kk = sg > 0 ? k : kV - 1 - k;
+                    V4 *q = reinterpret_cast<V4 *>(img + (int64_t)(X0 + k) * pitch + y0);
+#pragma unroll
+                    for (int u = 0; u < NV; ++u) {
+                        V4 o;
+                        o.x = (DstE)v[4 * u + 0][kk];
+                        o.y = (DstE)v[4 * u + 1][kk];
+                        o.z = (DstE)v[4 * u + 2][kk];
+                        o.w = (DstE)v[4 * u + 3][kk];
+                        q[u] = o;
+                    }
+                }
+                return;
+            }
+#pragma unroll
+            for (int k0 = 0; k0 < kV; k0 += kB) {
+                V4 old[kB][NV];
+#pragma unroll
+                for (int j = 0; j < kB; ++j)
+#pragma unroll
+                    for (int u = 0; u < NV; ++u)
+                        old[j][u] = reinterpret_cast<const V4 *>(
+                            img + (int64_t)(X0 + k0 + j) * pitch + y0)[u];
+#pragma unroll
+                for (int j = 0; j < kB; ++j) {
+                    const int k = k0 + j;
+                    const int kk = sg > 0 ? k : kV - 1 - k;
+                    V4 *q = reinterpret_cast<V4 *>(img + (int64_t)(X0 + k) * pitch + y0);
+#pragma unroll
+                    for (int u = 0; u < NV; ++u) {
+                        V4 o = old[j][u];
+                        o.x = (DstE)Arith<Acc>::add((Acc)o.x, v[4 * u + 0][kk]);
+                        o.y = (DstE)Arith<Acc>::add((Acc)o.y, v[4 * u + 1][kk]);
+                        o.z = (DstE)Arith<Acc>::add((Acc)o.z, v[4 * u + 2][kk]);
+                        o.w = (DstE)Arith<Acc>::add((Acc)o.w, v[4 * u + 3][kk]);
+                        q[u] = o;
+                    }
                 }
             }
-        }
-        return;
-    }
-    // transposed: image row X, image columns y0 .. y0 + R - 1
+        } else {
 #pragma unroll
-    for (int k = 0; k < kV; ++k) {
-        const int p = lo + k;
-        if (p < p_lo || p >= p_hi) continue;
-        const int X = X0 + k;
-        Acc col[R];   // column k in ascending p order (selects, no dynamic indexing)
+            for (int k = 0; k < kV; ++k) {
+                const int p = lo + k;
+                if (p < p_lo || p >= p_hi) continue;
+                Vec8<Acc> col;
 #pragma unroll
-        for (int r = 0; r < R; ++r) col[r] = sg > 0 ? v[r][k] : v[r][kV - 1 - k];
-        DstE *row = img + (int64_t)X * pitch;
-        if constexpr (R >= 4) {
-            DstE *q4 = row + y0;
-            if (y0 + R <= d.dst_h && (reinterpret_cast<uintptr_t>(q4) & 15) == 0) {
-                using V4 = typename std::conditional<std::is_same<DstE, float>::value, float4,
-                                                     int4>::type;
-#pragma unroll
-                for (int j = 0; j < R / 4; ++j) {
-                    V4 q;
-                    if (acc) q = reinterpret_cast<const V4 *>(q4)[j];
-                    else q.x = q.y = q.z = q.w = DstE(0);
-                    q.x = acc_store<DstE, Acc>(q.x, col[4 * j + 0], acc);
-                    q.y = acc_store<DstE, Acc>(q.y, col[4 * j + 1], acc);
-                    q.z = acc_store<DstE, Acc>(q.z, col[4 * j + 2], acc);
-                    q.w = acc_store<DstE, Acc>(q.w, col[4 * j + 3], acc);
-                    reinterpret_cast<V4 *>(q4)[j] = q;
-                }
-                continue;
+                for (int r = 0; r < kV; ++r)
+                    col.x[r] = r < R ? (sg > 0 ? v[r < R ? r : 0][k] : v[r < R ? r : 0][kV - 1 - k])
+                                     : Acc(0);
+                store_image_col_edge<R, Acc, DstE>(img + (int64_t)(X0 + k) * pitch, y0, d.dst_h,
+                                                   acc, col);
             }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int y = y0 + r;
-            if (y < d.dst_h) row[y] = acc_store<DstE, Acc>(row[y], col[r], acc);
         }
     }
 }
@@ -676,7 +778,7 @@ struct ItemPos {
     bool black;
 };
 
-template <int M, int SG, bool ADJ, bool FIN>
+template <int M, int SG, bool ADJ, int FIN>
 __device__ __forceinline__ ItemPos item_pos(const PassDesc &d, int T, int gy, int tile) {
     ItemPos ip;
     ip.S = gy / d.a_count;
@@ -729,7 +831,7 @@ __device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &
 // Block B of a two-block item: level-MA slope a2 of every mini-strip g, read
 // from the shared tile with the shear a2*g, MB more levels, then the
 // destination (zeros for a black tile, without reading the tile).
-template <int MA, int MB, int SG, bool ADJ, bool FIN, typename Acc, typename MidE, typename DstE>
+template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename MidE, typename DstE>
 __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &G,
                                              const ItemPos &ip, const MidE *sm, int warp,
                                              int nwarps, int lane) {
@@ -767,7 +869,7 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
         if (lane < kLanesValid && i0 < T) {
             const DestCols dc = dest_cols<SG, FIN, Acc, DstE>(d, ip.D, i0);
             if constexpr (ADJ && FIN) {
-                store_image_block<SG, RB, Acc, DstE>(d, hi_row(d, M, ip.S, ip.a, a2 * RB), dc.lo,
+                store_image_block<SG, FIN == 2, RB, Acc, DstE>(d, hi_row(d, M, ip.S, ip.a, a2 * RB), dc.lo,
                                                      v);
             } else {
                 store_rows<SG, FIN, RB, Acc, DstE>(d, dc, hi_row(d, M, ip.S, ip.a, a2 * RB), v);
@@ -780,10 +882,10 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
 // block A, a CTA barrier, block B.
 // ADJ selects the adjoint form at compile time (cyclic columns, row-mapped
 // gradient source, image-gradient destination) so the forward kernels carry
-// none of its code; FIN likewise selects the final level's destination (the
-// caller's layout) over an intermediate level, so each kernel holds one store
-// path.
-template <int MA, int MB, int SG, bool ADJ, bool FIN, typename Acc, typename SrcE, typename MidE,
+// none of its code; FIN likewise selects the destination (0 an intermediate
+// level, 1 the caller's layout, 2 an adjoint's transposed image gradient), so
+// each kernel holds one store path.
+template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm) {
     constexpr int M = MA + MB, RA = 1 << MA;
@@ -812,7 +914,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             if (lane < kLanesValid && i0 < T) {
                 const DestCols dc = dest_cols<SG, FIN, Acc, DstE>(d, ip.D, i0);
                 if constexpr (ADJ && FIN) {
-                    store_image_block<SG, RA, Acc, DstE>(d, hi_row(d, M, ip.S, ip.a, 0), dc.lo, v);
+                    store_image_block<SG, FIN == 2, RA, Acc, DstE>(d, hi_row(d, M, ip.S, ip.a, 0), dc.lo, v);
                 } else {
                     store_rows<SG, FIN, RA, Acc, DstE>(d, dc, hi_row(d, M, ip.S, ip.a, 0), v);
                 }

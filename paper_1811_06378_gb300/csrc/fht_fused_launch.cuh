@@ -44,9 +44,10 @@ inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t 
     return rd + wr;
 }
 
-// SG is the pass's sign in buffer coordinates (+1 or -1) and FIN whether it
-// writes the final level, both fixed at compile time.
-template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+// SG is the pass's sign in buffer coordinates (+1 or -1) and FIN what it
+// writes (0 an intermediate level, 1 the final level, 2 the final level of
+// an adjoint into a transposed image gradient), both fixed at compile time.
+template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
     fused_forward_kernel(PassDesc d) {
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
 }
 
-template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
     fused_adjoint_kernel(PassDesc d) {
@@ -83,7 +84,7 @@ unsigned int read_reset_pipe_timeouts() {
 const bool g_pipe_counter_registered = register_device_counter(&read_reset_pipe_timeouts);
 }  // namespace
 
-template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     fused_pipe_forward_kernel(PassDesc d, int n_items, size_t tile_bytes) {
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
                                                               bars, &g_pipe_timeouts);
 }
 
-template <int MA, int MB, int SG, bool FIN, typename Acc, typename SrcE, typename MidE,
+template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     fused_pipe_adjoint_kernel(PassDesc d, int n_items, size_t tile_bytes) {
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
                                                              bars, &g_pipe_timeouts);
 }
 
-template <int MA, int MB, bool ADJ, bool FIN, typename Acc, typename SrcE, typename MidE,
+template <int MA, int MB, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 void (*pipe_kernel_ptr(int sigma))(PassDesc, int, size_t) {
     if constexpr (ADJ) {
@@ -125,7 +126,7 @@ struct FinCases {
     static constexpr bool kFinal = !std::is_same<DstE, uint16_t>::value;
 };
 
-template <int MA, int MB, bool ADJ, bool FIN, typename Acc, typename SrcE, typename MidE,
+template <int MA, int MB, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 void (*fused_kernel_ptr(int sigma))(PassDesc) {
     if constexpr (ADJ) {
@@ -161,9 +162,14 @@ cudaError_t launch_pipe_t(PassDesc d, cudaStream_t st) {
     using FC = FinCases<ADJ, SrcE, DstE>;
     void (*k)(PassDesc, int, size_t) = nullptr;
     if (d.hi_final) {
-        if constexpr (FC::kFinal) k = pipe_kernel_ptr<MA, MB, ADJ, true, Acc, SrcE, MidE, DstE>(d.sigma);
+        if constexpr (FC::kFinal) {
+            if constexpr (ADJ) {
+                if (d.dst_transpose) k = pipe_kernel_ptr<MA, MB, ADJ, 2, Acc, SrcE, MidE, DstE>(d.sigma);
+            }
+            if (!k) k = pipe_kernel_ptr<MA, MB, ADJ, 1, Acc, SrcE, MidE, DstE>(d.sigma);
+        }
     } else {
-        if constexpr (FC::kLevel) k = pipe_kernel_ptr<MA, MB, ADJ, false, Acc, SrcE, MidE, DstE>(d.sigma);
+        if constexpr (FC::kLevel) k = pipe_kernel_ptr<MA, MB, ADJ, 0, Acc, SrcE, MidE, DstE>(d.sigma);
     }
     if (!k) return cudaErrorInvalidValue;   // a type combination no plan produces
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -211,9 +217,14 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     using FC = FinCases<ADJ, SrcE, DstE>;
     void (*k)(PassDesc) = nullptr;
     if (d.hi_final) {
-        if constexpr (FC::kFinal) k = fused_kernel_ptr<MA, MB, ADJ, true, Acc, SrcE, MidE, DstE>(d.sigma);
+        if constexpr (FC::kFinal) {
+            if constexpr (ADJ) {
+                if (d.dst_transpose) k = fused_kernel_ptr<MA, MB, ADJ, 2, Acc, SrcE, MidE, DstE>(d.sigma);
+            }
+            if (!k) k = fused_kernel_ptr<MA, MB, ADJ, 1, Acc, SrcE, MidE, DstE>(d.sigma);
+        }
     } else {
-        if constexpr (FC::kLevel) k = fused_kernel_ptr<MA, MB, ADJ, false, Acc, SrcE, MidE, DstE>(d.sigma);
+        if constexpr (FC::kLevel) k = fused_kernel_ptr<MA, MB, ADJ, 0, Acc, SrcE, MidE, DstE>(d.sigma);
     }
     if (!k) return cudaErrorInvalidValue;   // a type combination no plan produces
     if (smem > 48 * 1024) {

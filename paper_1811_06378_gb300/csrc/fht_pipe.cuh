@@ -75,7 +75,7 @@ __host__ __device__ inline size_t pipe_tile_bytes(const TileGeom &G, int MA, int
     return (b + 127) & ~(size_t)127;
 }
 
-template <int MA, int MB, int SG, bool ADJ, bool FIN, typename Acc, typename SrcE, typename MidE,
+template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __device__ __forceinline__ void pipe_items(const PassDesc &d, int n_items, size_t tile_bytes,
                                            unsigned char *smem, uint64_t *bars,
