@@ -195,7 +195,10 @@ __device__ __forceinline__ void reverse8(Acc (&v)[kV]) {
 }
 
 // Store 8 ascending elements at row[lo..lo+7], dropping those outside [0, cols).
-template <typename E, typename Acc>
+// kStream marks data no later pass of this transform reads (the final level):
+// its vector stores are evict-first in L2, so they displace less of the
+// intermediate level the pass is reading.
+template <typename E, typename Acc, bool kStream = false>
 __device__ __forceinline__ void store8(E *row, int lo, int cols, const Acc (&v)[kV]) {
     E *p = row + lo;
     if (lo >= 0 && lo + kV <= cols && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
@@ -205,14 +208,20 @@ __device__ __forceinline__ void store8(E *row, int lo, int cols, const Acc (&v)[
             q.y = pack_u16x2((uint32_t)v[2], (uint32_t)v[3]);
             q.z = pack_u16x2((uint32_t)v[4], (uint32_t)v[5]);
             q.w = pack_u16x2((uint32_t)v[6], (uint32_t)v[7]);
-            *reinterpret_cast<uint4 *>(p) = q;
+            if constexpr (kStream) __stcs(reinterpret_cast<uint4 *>(p), q);
+            else *reinterpret_cast<uint4 *>(p) = q;
         } else {
             using V4 = typename std::conditional<std::is_same<E, float>::value, float4, int4>::type;
             V4 a, b;
             a.x = (E)v[0]; a.y = (E)v[1]; a.z = (E)v[2]; a.w = (E)v[3];
             b.x = (E)v[4]; b.y = (E)v[5]; b.z = (E)v[6]; b.w = (E)v[7];
-            reinterpret_cast<V4 *>(p)[0] = a;
-            reinterpret_cast<V4 *>(p)[1] = b;
+            if constexpr (kStream) {
+                __stcs(reinterpret_cast<V4 *>(p), a);
+                __stcs(reinterpret_cast<V4 *>(p) + 1, b);
+            } else {
+                reinterpret_cast<V4 *>(p)[0] = a;
+                reinterpret_cast<V4 *>(p)[1] = b;
+            }
         }
     } else {
         Vec8<Acc> r;
@@ -553,7 +562,7 @@ __device__ __forceinline__ void store_rows(const PassDesc &d, const DestCols &c,
 #pragma unroll
         for (int k = 0; k < kV; ++k) asc[k] = SG > 0 ? v[r][k] : v[r][kV - 1 - k];
         if (c.vec) {
-            store8<DstE, Acc>(row + r * stride, c.X0, c.X0 + kV, asc);
+            store8<DstE, Acc, true>(row + r * stride, c.X0, c.X0 + kV, asc);
         } else {
             Vec8<Acc> e;
 #pragma unroll
