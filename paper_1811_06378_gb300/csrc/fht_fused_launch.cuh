@@ -47,9 +47,16 @@ inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t 
 // SG is the pass's sign in buffer coordinates (+1 or -1) and FIN what it
 // writes (0 an intermediate level, 1 the final level, 2 the final level of
 // an adjoint into a transposed image gradient), both fixed at compile time.
+// CTAs per SM the register budget is sized for: three with a 2-byte shared
+// tile (its 51 KB fits three times), else two.
+template <typename MidE>
+constexpr int fused_min_blocks() {
+    return sizeof(MidE) == 2 ? 24 / kFusedWarps : 16 / kFusedWarps;
+}
+
 template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
-__global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
+__global__ void __launch_bounds__(kFusedWarps * 32, fused_min_blocks<MidE>())
     fused_forward_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_forward_item<MA, MB, SG, false, FIN, Acc, SrcE, MidE, DstE>(
