@@ -91,6 +91,10 @@ def test_bad_arguments_rejected_on_host(fht):
     assert L.fht_forward(fake, U8, 8, -1, 8, 0, fake, I32, 16, null, 0, st) == EINVAL
     assert L.fht_forward(fake, U8, 8, 8, 8, 4, fake, I32, 16, null, 0, st) == EINVAL
     assert L.fht_forward(fake, U8, 1 << 20, 8, 8, 0, fake, I32, 16, null, 0, st) == EINVAL
+    # the largest padded side is 2^15: 32769 rows pad to 2^16
+    big = 8 + (1 << 16)
+    assert L.fht_forward(fake, U8, 32769, 8, 8, 0, fake, I32, big, fake, 1 << 40, st) == EINVAL
+    assert L.fht_forward(fake, U8, 8, 32769, 32769, 2, fake, I32, big, fake, 1 << 40, st) == EINVAL
     # pitches
     assert L.fht_forward(fake, U8, 8, 8, 7, 0, fake, I32, 16, null, 0, st) == EINVAL
     assert L.fht_forward(fake, U8, 8, 8, 8, 0, fake, I32, 15, null, 0, st) == EINVAL

@@ -343,6 +343,33 @@ def test_range_pruning_matches_full_rows(fht, h, w, q):
         assert torch.equal(got, full[t_lo:t_hi + 1]), (t_lo, t_hi)
 
 
+
+@pytest.mark.parametrize("h,w,q,kind", [(32768, 300, 0, "u8"), (300, 32768, 2, "u8"),
+                                        (32768, 200, 1, "f32")])
+def test_max_size_32768_sampled(fht, h, w, q, kind):
+    """The largest supported quadrant (n = 32768 = 2^15: three passes of five
+    levels, a uint16 level and then an int32 level for uint8 images): sampled
+    outputs, the corners included, against the oracle's single-point sums
+    (exact for integers, within 1e-5 * sum|I| for FP32)."""
+    img = edges_and_lines(h, w, seed=15) if kind == "u8" else random_image(h, w, "f32", seed=15)
+    acc = torch.int32 if kind == "u8" else torch.float32
+    H = fht.forward(dev(img), q, acc=acc)
+    n, Wq = H.shape
+    assert n == 32768
+    rng = np.random.default_rng(q)
+    ts, xs = rng.integers(0, n, 300), rng.integers(0, Wq, 300)
+    ts[:4] = [0, n - 1, 0, n - 1]
+    xs[:4] = [0, 0, Wq - 1, Wq - 1]
+    got = H[torch.from_numpy(ts).cuda(), torch.from_numpy(xs).cuda()].cpu().numpy()
+    want = O.points(img, q, ts, xs)
+    if kind == "u8":
+        assert (got == want).all()
+    else:
+        mass = float(np.abs(img.astype(np.float64)).sum())
+        assert np.abs(got.astype(np.float64) - want).max() <= FP32_TOL * mass
+    del H
+    torch.cuda.empty_cache()
+
 def test_zz_no_pipelined_wait_timed_out(fht):
     """Every pipelined pass run by this module finished all its hand-offs
     (runs last in the module: the count covers all the launches above)."""
