@@ -224,11 +224,11 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
  * against the plan; workspace is >= workspace_bytes, 256-byte aligned. One
  * host-to-device copy of the tables, one memset and one kernel launch on
  * `stream`, all capturable in a CUDA graph. The descriptors are staged in
- * pinned host memory owned by the plan, one table for direct calls and one
- * for the latest capture: a graph replays the descriptors given when it was
- * captured until the plan is captured again, and a direct call first waits
- * until the previous direct call's copy of its table has run. A plan serves
- * one stream at a time. */
+ * pinned host memory owned by the plan: three tables used in turn by direct
+ * calls (a call first waits until the copy of the call that used its table
+ * last has run) and one for the latest capture (a graph replays the
+ * descriptors given when it was captured until the plan is captured again).
+ * A plan serves one stream at a time. */
 fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void *workspace,
                                size_t workspace_bytes, void *stream);
 

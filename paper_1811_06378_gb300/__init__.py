@@ -17,6 +17,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 __all__ = [
@@ -265,11 +266,6 @@ def adjoint(grad: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: in
 
 # ------------------------------------------------------------------ batched
 
-class _ImageDesc(ctypes.Structure):
-    _fields_ = [("img", ctypes.c_void_p), ("img_pitch", ctypes.c_int64),
-                ("out", ctypes.c_void_p), ("out_pitch", ctypes.c_int64)]
-
-
 class BatchPlan:
     """Many images of different sizes, each transformed as `forward` would
     (one quadrant, one type pair), in one persistent launch."""
@@ -289,6 +285,19 @@ class BatchPlan:
         self._plan = plan
         self.workspace_bytes = nbytes.value
         self.out_shapes = [query_shape(h, w, q) for h, w in self.shapes]
+        self._in_sizes = [torch.Size(sh) for sh in self.shapes]
+        self._out_sizes = [torch.Size(sh) for sh in self.out_shapes]
+
+    def _reject(self, j, x, o):
+        """Raise the precise error for image j / output j."""
+        _dev2d(x, "img")
+        _dev2d(o, "out")
+        if tuple(x.shape) != self.shapes[j] or x.dtype != self.in_dtype:
+            raise ValueError(f"image {j}: expected {self.shapes[j]} {self.in_dtype}")
+        _shape(o, self.out_shapes[j], f"out[{j}]")
+        if o.dtype != self.acc:
+            raise ValueError(f"out[{j}] must be {self.acc}")
+        raise ValueError(f"image {j} or out[{j}] is not a usable 2-D CUDA tensor")
 
     def workspace(self, device) -> torch.Tensor:
         return torch.empty(max(self.workspace_bytes, 1), dtype=torch.uint8, device=device)
@@ -300,20 +309,21 @@ class BatchPlan:
         dev = imgs[0].device
         if outs is None:
             outs = [torch.empty(sh, dtype=self.acc, device=dev) for sh in self.out_shapes]
-        descs = (_ImageDesc * len(imgs))()
+        rows = []
         for j, (x, o) in enumerate(zip(imgs, outs)):
-            it, ip = _dev2d(x, "img")
-            ot, op = _dev2d(o, "out")
-            if tuple(x.shape) != self.shapes[j] or x.dtype != self.in_dtype:
-                raise ValueError(f"image {j}: expected {self.shapes[j]} {self.in_dtype}")
-            _shape(o, self.out_shapes[j], f"out[{j}]")
-            if o.dtype != self.acc:
-                raise ValueError(f"out[{j}] must be {self.acc}")
-            descs[j] = _ImageDesc(x.data_ptr(), ip, o.data_ptr(), op)
+            xs, os_ = x.stride(), o.stride()
+            if (x.dtype != self.in_dtype or o.dtype != self.acc or not x.is_cuda
+                    or not o.is_cuda or x.shape != self._in_sizes[j]
+                    or o.shape != self._out_sizes[j] or xs[1] != 1 or os_[1] != 1):
+                self._reject(j, x, o)
+            rows.append((x.data_ptr(), max(xs[0], x.shape[1]),
+                         o.data_ptr(), max(os_[0], o.shape[1])))
+        # fht_image_desc is {img, img_pitch, out, out_pitch}, 8 bytes each
+        descs = np.array(rows, dtype=np.int64)
         ws = self.workspace(dev) if workspace is None else workspace
         if ws.numel() * ws.element_size() < self.workspace_bytes:
             raise ValueError("workspace too small")
-        _check(lib.fht_forward_batched(self._plan, ctypes.cast(descs, ctypes.c_void_p),
+        _check(lib.fht_forward_batched(self._plan, ctypes.c_void_p(descs.ctypes.data),
                                        _ptr(ws), _nbytes(ws), _stream(stream)),
                "fht_forward_batched")
         self._last_ws = ws

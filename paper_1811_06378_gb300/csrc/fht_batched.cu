@@ -23,6 +23,10 @@
 using namespace fht;
 using namespace fht::batched;
 
+// Direct launches of one plan stage their segment tables in turn in this
+// many pinned tables, so the host can run that many launches ahead.
+constexpr int kDirectTables = 3;
+
 struct fht_plan {
     int count = 0;
     int f32 = 0;
@@ -32,11 +36,13 @@ struct fht_plan {
     size_t ws_bytes = 0, smem = 0;
     int n_done = 0;
     std::vector<int> h, w, rows, cols;   // per image: size, and its quadrant's n x W
-    // pinned staging of the segment table: [0, counters_off) for direct
-    // launches, [counters_off, 2 counters_off) for the latest stream capture
+    // pinned staging of the segment table: kDirectTables tables used in turn
+    // by direct launches (each reused only once its previous copy has run),
+    // then one for the latest stream capture
     void *host_table = nullptr;
-    cudaEvent_t copied = nullptr;   // after the last direct launch's table copy
-    bool copy_pending = false;
+    cudaEvent_t copied[kDirectTables] = {};   // after each direct table's last copy
+    bool copy_pending[kDirectTables] = {};
+    int next_table = 0;
     long long wait_budget = 4000000000LL;   // ~2 s of SM clocks
     int dep_bias = 0;
 };
@@ -144,6 +150,8 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
             s.variant = f32 ? kVarF32 : (p == 0 ? (npass == 1 ? kVarU8Final : kVarU8Level)
                                                 : kVarU16Final);
             s.tiles = d.tiles;
+            s.units = d.s_count * d.a_count * d.tiles;
+            s.chunk = std::max(1, std::min(kUnitsPerItem, s.units));
             s.lo_from_image = p == 0;
             s.hi_from_image = d.hi_final;
             s.lo_off = (int64_t)lvl_off;
@@ -151,7 +159,7 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
             s.done_index = n_done + p;
             s.dep_index = p == 0 ? -1 : n_done + p - 1;
             s.dep_count = prev_items;
-            prev_items = d.s_count * d.a_count * d.tiles;
+            prev_items = (s.units + s.chunk - 1) / s.chunk;
             pend.push_back(Pending{s, p});
         }
         n_done += npass;
@@ -165,7 +173,7 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
     int items = 0;
     for (auto &pd : pend) {
         pd.s.item_begin = items;
-        items += pd.s.d.s_count * pd.s.d.a_count * pd.s.tiles;
+        items += (pd.s.units + pd.s.chunk - 1) / pd.s.chunk;
         segs.push_back(pd.s);
     }
     fht_plan *P = new (std::nothrow) fht_plan();
@@ -195,18 +203,19 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
         P->rows.push_back(r);
         P->cols.push_back(c);
     }
-    if (cudaMallocHost(&P->host_table, 2 * P->counters_off) != cudaSuccess) {
+    if (cudaMallocHost(&P->host_table, (kDirectTables + 1) * P->counters_off) != cudaSuccess) {
         cudaGetLastError();
         delete P;
         return FHT_ENOMEM;
     }
-    if (cudaEventCreateWithFlags(&P->copied, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFreeHost(P->host_table);
-        delete P;
-        return FHT_ECUDA;
+    for (int c = 0; c < kDirectTables; ++c) {
+        if (cudaEventCreateWithFlags(&P->copied[c], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            fht_plan_destroy(P);
+            return FHT_ECUDA;
+        }
     }
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c <= kDirectTables; ++c)
         std::memcpy(static_cast<unsigned char *>(P->host_table) + c * P->counters_off,
                     segs.data(), P->table_bytes);
     *plan = P;
@@ -228,14 +237,18 @@ fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FHT_ECUDA;
     const bool capturing = cs != cudaStreamCaptureStatusNone;
-    // the previous direct launch's copy must have read the table before it
-    // is rewritten
-    if (!capturing && plan->copy_pending) {
-        if (cudaEventSynchronize(plan->copied) != cudaSuccess) return FHT_ECUDA;
-        plan->copy_pending = false;
+    // a direct launch takes the next table of the ring, once the copy of the
+    // launch that used it last has read it
+    const int tab = capturing ? kDirectTables : plan->next_table;
+    if (!capturing) {
+        plan->next_table = (plan->next_table + 1) % kDirectTables;
+        if (plan->copy_pending[tab]) {
+            if (cudaEventSynchronize(plan->copied[tab]) != cudaSuccess) return FHT_ECUDA;
+            plan->copy_pending[tab] = false;
+        }
     }
-    unsigned char *table =
-        static_cast<unsigned char *>(plan->host_table) + (capturing ? plan->counters_off : 0);
+    unsigned char *table = static_cast<unsigned char *>(plan->host_table) +
+                           (size_t)tab * plan->counters_off;
     BatchSeg *segs = reinterpret_cast<BatchSeg *>(table);
     for (int i = 0; i < plan->n_segs; ++i) {
         BatchSeg &sg = segs[i];
@@ -255,8 +268,8 @@ fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void
     }
     cudaError_t e = cudaMemcpyAsync(ws, table, plan->counters_off, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !capturing) {
-        e = cudaEventRecord(plan->copied, st);
-        if (e == cudaSuccess) plan->copy_pending = true;
+        e = cudaEventRecord(plan->copied[tab], st);
+        if (e == cudaSuccess) plan->copy_pending[tab] = true;
     }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ws + plan->counters_off, 0,
@@ -306,9 +319,10 @@ fht_status fht_batched_test_hooks(fht_plan *plan, long long wait_budget_cycles, 
 
 void fht_plan_destroy(fht_plan *plan) {
     if (!plan) return;
-    if (plan->copied) {
-        if (plan->copy_pending) cudaEventSynchronize(plan->copied);
-        cudaEventDestroy(plan->copied);
+    for (int c = 0; c < kDirectTables; ++c) {
+        if (!plan->copied[c]) continue;
+        if (plan->copy_pending[c]) cudaEventSynchronize(plan->copied[c]);
+        cudaEventDestroy(plan->copied[c]);
     }
     if (plan->host_table) cudaFreeHost(plan->host_table);
     delete plan;

@@ -15,6 +15,13 @@ namespace batched {
 constexpr int kWarps = 8;
 constexpr int kMaxBatchK = 12;   // images up to 4096 rows (transposed: columns)
 constexpr int kMaxSegsShared = 2048;   // segment keys kept in shared memory
+// (group, tile) units per claimed item: the per-item bookkeeping (claim,
+// segment search, descriptor copy, dependency check, release) is paid once
+// for several units
+#ifndef FHT_BATCH_UNITS
+#define FHT_BATCH_UNITS 4
+#endif
+constexpr int kUnitsPerItem = FHT_BATCH_UNITS;
 
 // Kernel variants. uint8 -> int32: single-pass images, first passes into a
 // uint16 level, and int32 final passes from it. float: one variant per M.
@@ -24,6 +31,8 @@ struct BatchSeg {
     PassDesc d;          // complete; lo/hi pointers and pitches written by the host per call
     int image, variant, m;
     int item_begin, tiles;
+    int units;           // (group, tile) units of the segment: s_count * a_count * tiles
+    int chunk;           // consecutive units one item covers
     int done_index;      // counter of this (image, pass)
     int dep_index;       // counter of (image, pass - 1), or -1
     int dep_count;       // items of (image, pass - 1)
@@ -80,7 +89,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
     batched_forward_kernel(const BatchSeg *segs, int n_segs, int total_items, Counters *ctr,
                            unsigned int *done, long long wait_budget, int dep_bias) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_item, s_skip, s_m, s_variant, s_tiles, s_first, s_done;
+    __shared__ int s_item, s_skip, s_m, s_variant, s_tiles, s_first, s_done, s_units, s_chunk;
     __shared__ int s_seg;
     __shared__ PassDesc s_desc;   // the current item's pass
     __shared__ int s_begin[kMaxSegsShared];   // segment start items, for the search
@@ -111,6 +120,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
                 s_tiles = sg.tiles;
                 s_first = sg.item_begin;
                 s_done = sg.done_index;
+                s_units = sg.units;
+                s_chunk = sg.chunk;
                 int skip = 0;
                 if (sg.dep_index >= 0) {
                     const unsigned int need = (unsigned int)(sg.dep_count + dep_bias);
@@ -140,29 +151,34 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
         const bool skip = s_skip != 0;
         if (!skip) {
             const PassDesc &d = s_desc;
-            const int local = item - s_first, m = s_m;
-            const int gy = local / s_tiles, tile = local - gy * s_tiles;
-            if constexpr (F32) {
-                if (d.hi_final)
-                    run_item_m<SG, 1, float, float, float, float>(m, d, gy, tile, smem_raw);
-                else
-                    run_item_m<SG, 0, float, float, float, float>(m, d, gy, tile, smem_raw);
-            } else {
-                // a uint8 image is finished in one pass or goes to a uint16
-                // level; a uint16 level's pass is the last (two passes at most)
-                switch (s_variant) {
-                case kVarU8Final:
-                    run_item_m<SG, 1, int32_t, uint8_t, uint16_t, int32_t>(m, d, gy, tile,
-                                                                             smem_raw);
-                    break;
-                case kVarU8Level:
-                    run_item_m<SG, 0, int32_t, uint8_t, uint16_t, uint16_t>(m, d, gy, tile,
+            const int m = s_m, tiles = s_tiles;
+            const int u0 = (item - s_first) * s_chunk;
+            const int u1 = u0 + s_chunk < s_units ? u0 + s_chunk : s_units;
+            for (int u = u0; u < u1; ++u) {
+                if (u > u0) __syncthreads();   // the previous unit's reads of the shared tile
+                const int gy = u / tiles, tile = u - gy * tiles;
+                if constexpr (F32) {
+                    if (d.hi_final)
+                        run_item_m<SG, 1, float, float, float, float>(m, d, gy, tile, smem_raw);
+                    else
+                        run_item_m<SG, 0, float, float, float, float>(m, d, gy, tile, smem_raw);
+                } else {
+                    // a uint8 image is finished in one pass or goes to a uint16
+                    // level; a uint16 level's pass is the last (two passes at most)
+                    switch (s_variant) {
+                    case kVarU8Final:
+                        run_item_m<SG, 1, int32_t, uint8_t, uint16_t, int32_t>(m, d, gy, tile,
+                                                                              smem_raw);
+                        break;
+                    case kVarU8Level:
+                        run_item_m<SG, 0, int32_t, uint8_t, uint16_t, uint16_t>(m, d, gy, tile,
                                                                                smem_raw);
-                    break;
-                default:
-                    run_item_m<SG, 1, int32_t, uint16_t, int32_t, int32_t>(m, d, gy, tile,
-                                                                             smem_raw);
-                    break;
+                        break;
+                    default:
+                        run_item_m<SG, 1, int32_t, uint16_t, int32_t, int32_t>(m, d, gy, tile,
+                                                                              smem_raw);
+                        break;
+                    }
                 }
             }
         }

@@ -89,24 +89,22 @@ def test_batched_wait_timeout_is_reported(fht):
 
 
 def test_batched_back_to_back_calls_keep_their_descriptors(fht):
-    """Two direct calls on one plan and stream, different images and outputs,
+    """Five direct calls on one plan and stream, different images and outputs,
     no synchronisation between them: each launch uses its own call's
-    descriptors (the plan's staging table is not rewritten before the first
-    call's copy of it has run)."""
+    descriptors (the plan's staging tables, used in turn, are not rewritten
+    before the copy of the call that used them last has run)."""
     shapes = [(300, 200), (64, 700), (513, 90)]
-    a = [torch.from_numpy(x).cuda() for x in edge_batch(shapes, seed=21)]
-    b = [torch.from_numpy(x).cuda() for x in edge_batch(shapes, seed=22)]
+    sets = [[torch.from_numpy(x).cuda() for x in edge_batch(shapes, seed=21 + k)]
+            for k in range(5)]
     plan = fht.BatchPlan(shapes, 1)
     ws = plan.workspace("cuda")
     torch.cuda._sleep(50_000_000)   # keep the stream busy so the copies are still queued
-    oa = plan.forward(a, workspace=ws)
-    ob = plan.forward(b, workspace=ws)
+    outs = [plan.forward(imgs, workspace=ws) for imgs in sets]
     torch.cuda.synchronize()
     assert plan.status(ws) == 0
-    for x, o in zip(a, oa):
-        assert torch.equal(o, fht.forward(x, 1))
-    for x, o in zip(b, ob):
-        assert torch.equal(o, fht.forward(x, 1))
+    for imgs, o in zip(sets, outs):
+        for x, y in zip(imgs, o):
+            assert torch.equal(y, fht.forward(x, 1))
 
 
 def test_batched_graph_keeps_captured_descriptors(fht):
