@@ -435,9 +435,20 @@ def run_ours(args):
                 g = torch.stack([fht.adjoint(ri, n5, n5) for ri in r])
                 x5.sub_(1e-6 * g)
 
-        rows["gd_step_64x1024_f32"] = row_entry(
-            gd_step, B5 * (2 * n5 * n5 * 4 + 2 * R5 * W5 * 4), B5 * n5 * n5)
-        del xt, b5, x5
+        gd_alg = B5 * (2 * n5 * n5 * 4 + 2 * R5 * W5 * 4)
+        rows["gd_step_64x1024_f32_eager"] = row_entry(gd_step, gd_alg, B5 * n5 * n5)
+        # the same step replayed from a CUDA graph, as a training loop would run
+        # it: its 64 images' 1024 small launches then leave no host gaps
+        gd_stream = torch.cuda.Stream()
+        gd_graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(gd_stream):
+            gd_step()
+            gd_stream.synchronize()
+            with torch.cuda.graph(gd_graph, stream=gd_stream):
+                gd_step()
+        torch.cuda.synchronize()
+        rows["gd_step_64x1024_f32"] = row_entry(gd_graph.replay, gd_alg, B5 * n5 * n5)
+        del xt, b5, x5, gd_graph
 
     # ---- roofline of the dominant kernel (largest share of the profiled
     # step): the library's CUDA events on the launch stream give its launch
