@@ -432,7 +432,7 @@ def run_ours(args):
         def gd_step():
             with torch.no_grad():
                 r = fht.FHTFunction.apply(x5) - b5
-                g = torch.stack([fht.adjoint(ri, n5, n5) for ri in r])
+                g = fht.adjoint_many(r, n5, n5)
                 x5.sub_(1e-6 * g)
 
         gd_alg = B5 * (2 * n5 * n5 * 4 + 2 * R5 * W5 * 4)

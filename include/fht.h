@@ -194,6 +194,37 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
                        void *grad_img, int64_t out_pitch, void *workspace,
                        size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------ uniform batches
+ * `batch` transforms of the same size and layout in one launch per pass (the
+ * launch's third grid dimension is the image), so that many small images fill
+ * the GPU. Not in the paper; the differentiable path uses it for (B, h, w)
+ * tensors. FP32 only (images, Hough images and gradients are float32).
+ * Image b lies b * *_batch_stride ELEMENTS past image 0 (strides at least one
+ * image apart: h * in_pitch for images, rows * out_pitch for Hough images);
+ * 1 <= batch <= 65535. Layout FHT_LAYOUT_QUADRANT transforms quadrant q;
+ * FHT_LAYOUT_FULL the four quadrants as fht_full_quadrants (without
+ * fhtshift). Results equal the single-image calls bit for bit. */
+
+/* Workspace bytes of a uniform batch: for each image, the bytes
+ * fht_workspace_size(h, w, layout, q, FHT_F32, FHT_F32) returns, rounded up
+ * to a multiple of 256. */
+fht_status fht_workspace_size_many(int batch, int h, int w, fht_layout layout, fht_quadrant q,
+                                   size_t *bytes);
+
+/* Forward transform of a uniform batch: img -> out, as fht_forward (layout
+ * QUADRANT) or fht_full_quadrants (layout FULL) for every image. */
+fht_status fht_forward_many(const void *img, int batch, int64_t img_batch_stride, int h, int w,
+                            int64_t in_pitch, fht_layout layout, fht_quadrant q, void *out,
+                            int64_t out_batch_stride, int64_t out_pitch, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
+/* Adjoint of a uniform batch: grad_hough -> grad_img, as fht_adjoint for
+ * every image (grad_img fully overwritten). */
+fht_status fht_adjoint_many(const void *grad_hough, int batch, int64_t grad_batch_stride, int h,
+                            int w, fht_layout layout, fht_quadrant q, int64_t in_pitch,
+                            void *grad_img, int64_t img_batch_stride, int64_t out_pitch,
+                            void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------ batched
  * Many images of different sizes in one persistent launch. Each image is
  * transformed exactly as fht_forward would transform it (same quadrant and

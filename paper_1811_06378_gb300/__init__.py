@@ -25,6 +25,7 @@ __all__ = [
     "query_shape", "full_shape", "full_row_to_quadrant", "angle_to_slopes",
     "workspace_size", "forward", "forward_range", "full_quadrants", "fhtshift",
     "adjoint", "FHTFunction", "profile_begin", "profile_end", "launch_count", "device_status",
+    "workspace_size_many", "forward_many", "adjoint_many",
     "BatchPlan", "FHT_OK", "FHT_ETIMEOUT",
 ]
 
@@ -74,6 +75,9 @@ def _load() -> ctypes.CDLL:
         "fht_profile_end": (i, [vp, i, ip]),
         "fht_launch_count": (ctypes.c_longlong, []),
         "fht_device_status": (ctypes.c_int, []),
+        "fht_workspace_size_many": (i, [i, i, i, i, i, ctypes.POINTER(sz)]),
+        "fht_forward_many": (i, [vp, i, i64, i, i, i64, i, i, vp, i64, i64, vp, sz, vp]),
+        "fht_adjoint_many": (i, [vp, i, i64, i, i, i, i, i64, vp, i64, i64, vp, sz, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -381,12 +385,71 @@ def device_status() -> int:
     return int(lib.fht_device_status())
 
 
+# ------------------------------------------------------------ uniform batches
+
+def _dev3d(t: torch.Tensor, name: str) -> tuple[int, int]:
+    """(pitch, batch stride) in elements of a float32 (B, rows, cols) CUDA tensor."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise ValueError(f"{name} must be a float32 CUDA tensor")
+    if t.dim() != 3 or t.stride(2) != 1:
+        raise ValueError(f"{name} must be 3-D (batch, rows, cols) with unit column stride")
+    return max(t.stride(1), t.shape[2]), t.stride(0)
+
+
+def workspace_size_many(batch: int, h: int, w: int, layout: int = LAYOUT_FULL,
+                        q: int = Q0) -> int:
+    """Workspace bytes of forward_many / adjoint_many on `batch` h x w images."""
+    n = ctypes.c_size_t()
+    _check(lib.fht_workspace_size_many(batch, h, w, layout, q, ctypes.byref(n)),
+           "fht_workspace_size_many")
+    return n.value
+
+
+def forward_many(imgs: torch.Tensor, layout: int = LAYOUT_FULL, q: int = Q0,
+                 out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """FP32 transforms of a (B, h, w) batch of same-size images in one launch
+    per pass: (B, rows, cols), each as full_quadrants (layout FULL) or
+    forward of quadrant q (layout QUADRANT)."""
+    ip, ib = _dev3d(imgs, "imgs")
+    B, h, w = imgs.shape
+    rows, cols = full_shape(h, w) if layout == LAYOUT_FULL else query_shape(h, w, q)
+    if out is None:
+        out = torch.empty((B, rows, cols), dtype=torch.float32, device=imgs.device)
+    _shape(out, (B, rows, cols), "out")
+    op, ob = _dev3d(out, "out")
+    ws = _workspace(workspace, workspace_size_many(B, h, w, layout, q), imgs.device)
+    _check(lib.fht_forward_many(_ptr(imgs), B, ib, h, w, ip, layout, q, _ptr(out), ob, op,
+                                _ptr(ws), _nbytes(ws), _stream(stream)), "fht_forward_many")
+    return out
+
+
+def adjoint_many(grads: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: int = Q0,
+                 out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """Adjoints of a (B, rows, cols) batch of FP32 Hough-image gradients in
+    one launch per pass: (B, h, w)."""
+    gp, gb = _dev3d(grads, "grads")
+    B = grads.shape[0]
+    rows, cols = full_shape(h, w) if layout == LAYOUT_FULL else query_shape(h, w, q)
+    _shape(grads, (B, rows, cols), "grads")
+    if out is None:
+        out = torch.empty((B, h, w), dtype=torch.float32, device=grads.device)
+    _shape(out, (B, h, w), "out")
+    op, ob = _dev3d(out, "out")
+    ws = _workspace(workspace, workspace_size_many(B, h, w, layout, q), grads.device)
+    _check(lib.fht_adjoint_many(_ptr(grads), B, gb, h, w, layout, q, gp, _ptr(out), ob, op,
+                                _ptr(ws), _nbytes(ws), _stream(stream)), "fht_adjoint_many")
+    return out
+
+
 class FHTFunction(torch.autograd.Function):
     """Differentiable FP32 Hough transform: forward by the CUDA butterfly,
     backward by the hand-written adjoint kernels (its exact transpose).
 
     apply(x, layout=LAYOUT_FULL, q=Q0) for a float32 CUDA tensor x of shape
-    (h, w), or (B, h, w) for a batch (one library call per image)."""
+    (h, w), or (B, h, w) for a batch of same-size images (one launch per pass
+    for the whole batch)."""
 
     @staticmethod
     def forward(ctx, x: torch.Tensor, layout: int = LAYOUT_FULL, q: int = Q0):
@@ -401,11 +464,11 @@ class FHTFunction(torch.autograd.Function):
 
         if x.dim() == 2:
             return one(x)
-        return torch.stack([one(img) for img in x])
+        return forward_many(x, layout, q)
 
     @staticmethod
     def backward(ctx, g: torch.Tensor):
         g = g.contiguous()
         if g.dim() == 2:
             return adjoint(g, ctx.h, ctx.w, ctx.layout, ctx.q), None, None
-        return torch.stack([adjoint(gi, ctx.h, ctx.w, ctx.layout, ctx.q) for gi in g]), None, None
+        return adjoint_many(g, ctx.h, ctx.w, ctx.layout, ctx.q), None, None

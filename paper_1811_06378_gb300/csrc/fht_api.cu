@@ -269,9 +269,19 @@ namespace {
 // First passes over uint8 images keep their shared tile in uint16.
 bool acc_is_u16_mid(const QuadPlan &P, int p) { return p == 0 && P.in_elem == kU8 && P.acc_elem == kI32; }
 
+// A uniform batch of same-size transforms: image b's source, destination and
+// workspace lie b * src / dst / ws bytes past image 0's.
+struct Batch {
+    int count = 1;
+    int64_t src = 0, dst = 0, ws = 0;
+};
+
 PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &final_side,
-                   void *ws, const FinalMap &fm, int t_lo, int t_hi) {
+                   void *ws, const FinalMap &fm, int t_lo, int t_hi, const Batch &B = Batch{}) {
     PassDesc d{};
+    d.batch = B.count;
+    d.lo_bstride = p == 0 ? B.src : B.ws;
+    d.hi_bstride = p == P.npass - 1 ? B.dst : B.ws;
     d.lo_image = p == 0;
     d.transpose = P.transpose;
     if (p == 0) {
@@ -323,9 +333,9 @@ PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &fina
 
 fht_status run_forward(const QuadPlan &P, const Side &image, const Side &out,
                        const FinalMap &fm, int t_lo, int t_hi, int acc_elem, void *ws,
-                       cudaStream_t st) {
+                       cudaStream_t st, const Batch &B = Batch{}) {
     for (int p = 0; p < P.npass; ++p) {
-        PassDesc d = pass_desc(P, p, image, out, ws, fm, t_lo, t_hi);
+        PassDesc d = pass_desc(P, p, image, out, ws, fm, t_lo, t_hi, B);
         cudaError_t e = launch_forward(P.m[p], d, acc_elem, st);
         if (e != cudaSuccess) {
             g_last_cuda_error = (int)e;
@@ -340,11 +350,11 @@ fht_status run_forward(const QuadPlan &P, const Side &image, const Side &out,
 // (transposed) image and written, or added, into grad_img.
 fht_status run_adjoint(const QuadPlan &P, const Side &grad_img, const Side &grad_hough,
                        const FinalMap &fm, int acc_elem, int accumulate, void *ws,
-                       cudaStream_t st) {
+                       cudaStream_t st, const Batch &B = Batch{}) {
     for (int p = 0; p < P.npass; ++p) {
         // output rows y < h_c of the opposite-sign transform are the image rows
         PassDesc d = pass_desc(P, p, grad_hough, grad_img, ws, FinalMap{0, P.n - 1, 0, 1, 0, 0},
-                               0, P.h_c - 1);
+                               0, P.h_c - 1, B);
         if (p == 0) {
             d.transpose = 0;
             d.lo.cols = P.W;
@@ -706,6 +716,120 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
         Side gh{const_cast<void *>(grad_hough), in_pitch, acc, 0, P.W};
         fht_status s = run_adjoint(P, gi, gh, full_map(qq, hp, wp), acc, qq > 0 ? 1 : 0,
                                    workspace, st);
+        if (s != FHT_OK) return s;
+    }
+    return FHT_OK;
+}
+
+// ------------------------------------------------------------ uniform batches
+
+// Workspace of one image of a uniform FP32 batch: the forward's and the
+// adjoint's intermediate levels, rounded to 256 bytes.
+static fht_status many_image_ws(int h, int w, fht_layout layout, fht_quadrant q, size_t *bytes) {
+    size_t one = 0;
+    const fht_status s = fht_workspace_size(h, w, layout, q, FHT_F32, FHT_F32, &one);
+    if (s != FHT_OK) return s;
+    *bytes = (one + 255) / 256 * 256;
+    return FHT_OK;
+}
+
+static bool many_args_ok(int batch, int h, int w, fht_layout layout, fht_quadrant q) {
+    if (batch < 1 || batch > 65535 || !sizes_ok(h, w)) return false;
+    if (layout == FHT_LAYOUT_QUADRANT) return quadrant_ok(q);
+    return layout == FHT_LAYOUT_FULL;
+}
+
+fht_status fht_workspace_size_many(int batch, int h, int w, fht_layout layout, fht_quadrant q,
+                                   size_t *bytes) {
+    if (!bytes || !many_args_ok(batch, h, w, layout, q)) return FHT_EINVAL;
+    size_t one = 0;
+    const fht_status s = many_image_ws(h, w, layout, q, &one);
+    if (s != FHT_OK) return s;
+    *bytes = one * (size_t)batch;
+    return FHT_OK;
+}
+
+fht_status fht_forward_many(const void *img, int batch, int64_t img_batch_stride, int h, int w,
+                            int64_t in_pitch, fht_layout layout, fht_quadrant q, void *out,
+                            int64_t out_batch_stride, int64_t out_pitch, void *workspace,
+                            size_t workspace_bytes, void *stream) {
+    if (!img || !out || !many_args_ok(batch, h, w, layout, q) || in_pitch < w) return FHT_EINVAL;
+    int rows = 0, cols = 0;
+    const fht_status sq = layout == FHT_LAYOUT_FULL ? fht_full_shape(h, w, &rows, &cols)
+                                                    : fht_query_shape(h, w, q, &rows, &cols);
+    if (sq != FHT_OK || out_pitch < cols) return FHT_EINVAL;
+    // images and outputs of the batch must not overlap one another
+    if (batch > 1 && (img_batch_stride < (int64_t)h * in_pitch ||
+                      out_batch_stride < (int64_t)rows * out_pitch))
+        return FHT_EINVAL;
+    size_t one = 0;
+    fht_status s = many_image_ws(h, w, layout, q, &one);
+    if (s != FHT_OK) return s;
+    if (workspace_bytes < one * (size_t)batch || (one > 0 && !workspace)) return FHT_EINVAL;
+    Batch B;
+    B.count = batch;
+    B.src = img_batch_stride * 4;
+    B.dst = out_batch_stride * 4;
+    B.ws = (int64_t)one;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (layout == FHT_LAYOUT_QUADRANT) {
+        QuadPlan P = make_plan(h, w, q, false, kF32, kF32);
+        if (P.K > kMaxK) return FHT_EINVAL;
+        Side image{const_cast<void *>(img), in_pitch, kF32, P.h_c, P.w_c};
+        Side o{out, out_pitch, kF32, 0, P.W};
+        return run_forward(P, image, o, quadrant_map(0, P.n - 1), 0, P.n - 1, kF32, workspace,
+                           st, B);
+    }
+    const int hp = next_pow2(h), wp = next_pow2(w);
+    if (ilog2(hp) > kMaxK || ilog2(wp) > kMaxK) return FHT_EINVAL;
+    for (int qq = 0; qq < 4; ++qq) {
+        QuadPlan P = make_plan(h, w, qq, true, kF32, kF32);
+        Side image{const_cast<void *>(img), in_pitch, kF32, P.h_c, P.w_c};
+        Side o{out, out_pitch, kF32, 0, P.W};
+        const FinalMap fm = full_map(qq, hp, wp);
+        s = run_forward(P, image, o, fm, fm.t_first, fm.t_last, kF32, workspace, st, B);
+        if (s != FHT_OK) return s;
+    }
+    return FHT_OK;
+}
+
+fht_status fht_adjoint_many(const void *grad_hough, int batch, int64_t grad_batch_stride, int h,
+                            int w, fht_layout layout, fht_quadrant q, int64_t in_pitch,
+                            void *grad_img, int64_t img_batch_stride, int64_t out_pitch,
+                            void *workspace, size_t workspace_bytes, void *stream) {
+    if (!grad_hough || !grad_img || !many_args_ok(batch, h, w, layout, q) || out_pitch < w)
+        return FHT_EINVAL;
+    int rows = 0, cols = 0;
+    const fht_status sq = layout == FHT_LAYOUT_FULL ? fht_full_shape(h, w, &rows, &cols)
+                                                    : fht_query_shape(h, w, q, &rows, &cols);
+    if (sq != FHT_OK || in_pitch < cols) return FHT_EINVAL;
+    if (batch > 1 && (grad_batch_stride < (int64_t)rows * in_pitch ||
+                      img_batch_stride < (int64_t)h * out_pitch))
+        return FHT_EINVAL;
+    size_t one = 0;
+    fht_status s = many_image_ws(h, w, layout, q, &one);
+    if (s != FHT_OK) return s;
+    if (workspace_bytes < one * (size_t)batch || (one > 0 && !workspace)) return FHT_EINVAL;
+    Batch B;
+    B.count = batch;
+    B.src = grad_batch_stride * 4;
+    B.dst = img_batch_stride * 4;
+    B.ws = (int64_t)one;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (layout == FHT_LAYOUT_QUADRANT) {
+        QuadPlan P = make_plan(h, w, q, false, kF32, kF32, true);
+        if (P.K > kMaxK) return FHT_EINVAL;
+        Side gi{grad_img, out_pitch, kF32, P.h_c, P.w_c};
+        Side gh{const_cast<void *>(grad_hough), in_pitch, kF32, 0, P.W};
+        return run_adjoint(P, gi, gh, quadrant_map(0, P.n - 1), kF32, 0, workspace, st, B);
+    }
+    const int hp = next_pow2(h), wp = next_pow2(w);
+    if (ilog2(hp) > kMaxK || ilog2(wp) > kMaxK) return FHT_EINVAL;
+    for (int qq = 0; qq < 4; ++qq) {
+        QuadPlan P = make_plan(h, w, qq, true, kF32, kF32, true);
+        Side gi{grad_img, out_pitch, kF32, P.h_c, P.w_c};
+        Side gh{const_cast<void *>(grad_hough), in_pitch, kF32, 0, P.W};
+        s = run_adjoint(P, gi, gh, full_map(qq, hp, wp), kF32, qq > 0 ? 1 : 0, workspace, st, B);
         if (s != FHT_OK) return s;
     }
     return FHT_OK;

@@ -65,6 +65,11 @@ struct PassDesc {
     int tile_w;          // output columns per tile
     int tiles;           // tiles per group
     int n_a;             // fused kernel: block-A warp-columns per tile
+    // uniform batch: `batch` same-size transforms in one launch (blockIdx.z),
+    // image b's source and destination `b * lo_bstride` / `b * hi_bstride`
+    // bytes past lo.ptr / hi.ptr (0 and 1 for a single transform)
+    int batch;
+    int64_t lo_bstride, hi_bstride;
     int black_wc;        // content width w_c (black-zone test of the final level)
     // final level only: slope t is row row_base + row_dir*t of the output,
     // present for t in [t_first, t_last]

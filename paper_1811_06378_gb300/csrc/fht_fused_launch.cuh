@@ -123,6 +123,36 @@ void (*pipe_kernel_ptr(int sigma))(PassDesc, int, size_t) {
     }
 }
 
+// Uniform batch: image blockIdx.z of `d.batch` same-size transforms. The
+// CTA's pass descriptor, with that image's source and destination, lives in
+// shared memory (thread 0 writes it) and the item reads it there.
+template <int MA, int MB, int SG, int FIN, bool ADJ, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
+__global__ void __launch_bounds__(kFusedWarps * 32, fused_min_blocks<MidE>())
+    fused_batch_kernel(PassDesc d) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ PassDesc s_d;
+    if (threadIdx.x == 0) {
+        s_d = d;
+        s_d.lo.ptr = static_cast<char *>(d.lo.ptr) + (int64_t)blockIdx.z * d.lo_bstride;
+        s_d.hi.ptr = static_cast<char *>(d.hi.ptr) + (int64_t)blockIdx.z * d.hi_bstride;
+    }
+    __syncthreads();
+    fused_forward_item<MA, MB, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(
+        s_d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
+}
+
+template <int MA, int MB, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
+          typename DstE>
+void (*batch_kernel_ptr(int sigma))(PassDesc) {
+    return sigma > 0 ? fused_batch_kernel<MA, MB, 1, FIN, ADJ, Acc, SrcE, MidE, DstE>
+                     : fused_batch_kernel<MA, MB, -1, FIN, ADJ, Acc, SrcE, MidE, DstE>;
+}
+
+// Uniform batches are built for float transforms (the differentiable path).
+template <typename Acc, typename SrcE>
+constexpr bool kBatchable = std::is_same<Acc, float>::value && std::is_same<SrcE, float>::value;
+
 // Which final-level flags a type combination can take: uint16 is only ever an
 // intermediate level, and a uint8 image goes to int32 only in a single
 // (final) pass.
@@ -201,8 +231,12 @@ cudaError_t launch_pipe_t(PassDesc d, cudaStream_t st) {
 
 template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
 cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
+    if (d.batch < 1 || d.batch > 65535) return cudaErrorInvalidValue;
+    if constexpr (!kBatchable<Acc, SrcE>) {
+        if (d.batch > 1) return cudaErrorNotSupported;
+    }
     if constexpr (MB > 0) {
-        if (pipe_enabled()) {
+        if (pipe_enabled() && d.batch == 1) {
             const cudaError_t e = launch_pipe_t<MA, MB, ADJ, Acc, SrcE, MidE, DstE>(d, st);
             if (e != cudaErrorNotSupported) return e;
         }
@@ -219,11 +253,18 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     if (smem > kMaxTileSmem) return cudaErrorInvalidConfiguration;
     d.tile_w = G.tile_out;
     d.tiles = (d.p_count + G.tile_out - 1) / G.tile_out;
-    dim3 grid(d.tiles, d.s_count * d.a_count);
+    dim3 grid(d.tiles, d.s_count * d.a_count, d.batch);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     using FC = FinCases<ADJ, SrcE, DstE>;
     void (*k)(PassDesc) = nullptr;
-    if (d.hi_final) {
+    const int fin = !d.hi_final ? 0 : (ADJ && d.dst_transpose ? 2 : 1);
+    if (d.batch > 1) {
+        if constexpr (kBatchable<Acc, SrcE>) {
+            if (fin == 0) k = batch_kernel_ptr<MA, MB, ADJ, 0, Acc, SrcE, MidE, DstE>(d.sigma);
+            else if (fin == 1) k = batch_kernel_ptr<MA, MB, ADJ, 1, Acc, SrcE, MidE, DstE>(d.sigma);
+            else if constexpr (ADJ) k = batch_kernel_ptr<MA, MB, ADJ, 2, Acc, SrcE, MidE, DstE>(d.sigma);
+        }
+    } else if (d.hi_final) {
         if constexpr (FC::kFinal) {
             if constexpr (ADJ) {
                 if (d.dst_transpose) k = fused_kernel_ptr<MA, MB, ADJ, 2, Acc, SrcE, MidE, DstE>(d.sigma);
@@ -240,9 +281,10 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     char name[64];
-    snprintf(name, sizeof name, "%s_m%d_%s%s", ADJ ? "adjoint_fused" : "forward_fused",
-             MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "");
-    LaunchScope scope(name, st, pass_alg_bytes(d, MA + MB, sizeof(SrcE), sizeof(DstE)));
+    snprintf(name, sizeof name, "%s_m%d_%s%s%s", ADJ ? "adjoint_fused" : "forward_fused",
+             MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "", d.batch > 1 ? "_batch" : "");
+    LaunchScope scope(name, st,
+                      d.batch * pass_alg_bytes(d, MA + MB, sizeof(SrcE), sizeof(DstE)));
     k<<<grid, kFusedWarps * 32, smem, st>>>(d);
     scope.done();
     return cudaGetLastError();

@@ -7,6 +7,7 @@ import os
 import re
 
 import pytest
+import torch
 
 import oracle as O
 
@@ -119,6 +120,19 @@ def test_bad_arguments_rejected_on_host(fht):
     assert L.fht_adjoint(fake, U8, 8, 8, 0, 0, 16, fake, 8, null, 0, st) == EINVAL
     assert L.fht_adjoint(fake, F32, 8, 8, 0, 0, 15, fake, 8, null, 0, st) == EINVAL
     assert L.fht_adjoint(fake, F32, 8, 8, 0, 0, 16, fake, 7, null, 0, st) == EINVAL
+    # uniform batches: batch count, overlapping items, FP32 only (no other types exist here)
+    assert L.fht_forward_many(fake, 0, 64, 8, 8, 8, 1, 0, fake, 512, 16, null, 0, st) == EINVAL
+    assert L.fht_forward_many(fake, 65536, 64, 8, 8, 8, 1, 0, fake, 512, 16, null, 0, st) == EINVAL
+    assert L.fht_forward_many(fake, 2, 63, 8, 8, 8, 1, 0, fake, 512, 16, null, 0, st) == EINVAL
+    assert L.fht_forward_many(fake, 2, 64, 8, 8, 8, 1, 0, fake, 16 * 29 - 1, 16, null, 0,
+                              st) == EINVAL
+    assert L.fht_adjoint_many(fake, 2, 16 * 29, 8, 8, 1, 0, 16, fake, 63, 8, null, 0,
+                              st) == EINVAL
+    n = ctypes.c_size_t()
+    assert L.fht_workspace_size_many(0, 8, 8, 1, 0, ctypes.byref(n)) == EINVAL
+    assert L.fht_workspace_size_many(3, 100, 100, 1, 0, ctypes.byref(n)) == 0
+    one = fht.workspace_size(100, 100, fht.LAYOUT_FULL, 0, torch.float32, torch.float32)
+    assert n.value == 3 * ((one + 255) // 256 * 256)
     # geometry queries
     r = ctypes.c_int()
     assert L.fht_query_shape(0, 4, 0, ctypes.byref(r), ctypes.byref(r)) == EINVAL
