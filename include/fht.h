@@ -245,8 +245,9 @@ typedef struct {
 
 /* Plan a batch of `count` images with sizes hs[j] x ws[j] (HOST arrays).
  * Writes the plan (free with fht_plan_destroy) and the device workspace it
- * needs (intermediate levels of every image, the work tables and counters).
- * Allocates only host memory (pinned staging for the tables). */
+ * needs (intermediate levels of every image, the work tables and counters;
+ * for float32 plans enough for fht_adjoint_batched as well). Allocates only
+ * host memory (pinned staging for the tables). */
 fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_quadrant q,
                                    fht_dtype in_t, fht_dtype acc_t, fht_plan **plan,
                                    size_t *workspace_bytes);
@@ -261,6 +262,29 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
  * descriptors given when it was captured until the plan is captured again).
  * A plan serves one stream at a time. */
 fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void *workspace,
+                               size_t workspace_bytes, void *stream);
+
+/* Per-image arguments of fht_adjoint_batched. */
+typedef struct {
+    const void *grad_hough;     /* DEVICE pointer: gradient w.r.t. quadrant j, n_j x W_j
+                                   float32, read only */
+    int64_t grad_hough_pitch;   /* elements, >= W_j (fht_query_shape) */
+    void *grad_img;             /* DEVICE pointer: gradient w.r.t. image j, h_j x w_j
+                                   float32, fully overwritten */
+    int64_t grad_img_pitch;     /* elements, >= w_j */
+} fht_adjoint_desc;
+
+/* Adjoint of the batch (float32 plans only; FHT_EUNSUPPORTED otherwise):
+ * for every image j, grad_img = H_j^T grad_hough, the transpose of its
+ * quadrant transform, exactly (bit for bit) what fht_adjoint with layout
+ * FHT_LAYOUT_QUADRANT and the plan's quadrant computes. Not in the paper: the
+ * transform is linear and the back-projection is its transpose, used by
+ * gradient-based reconstruction over many images of different sizes. One
+ * persistent launch as fht_forward_batched (same staging, capture and status
+ * rules; descs is a HOST array of `count` descriptors, workspace >= the
+ * plan's workspace_bytes, 256-byte aligned, shared with the forward calls of
+ * the same stream). */
+fht_status fht_adjoint_batched(fht_plan *plan, const fht_adjoint_desc *descs, void *workspace,
                                size_t workspace_bytes, void *stream);
 
 /* Wait for `stream` and report the last batched launch's device status in

@@ -68,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "fht_plan_create_batched": (i, [ctypes.POINTER(i), ctypes.POINTER(i), i, i, i, i,
                                         ctypes.POINTER(vp), ctypes.POINTER(sz)]),
         "fht_forward_batched": (i, [vp, vp, vp, sz, vp]),
+        "fht_adjoint_batched": (i, [vp, vp, vp, sz, vp]),
         "fht_batched_status": (i, [vp, vp, vp]),
         "fht_batched_test_hooks": (i, [vp, ctypes.c_longlong, i]),
         "fht_plan_destroy": (None, [vp]),
@@ -272,7 +273,8 @@ def adjoint(grad: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: in
 
 class BatchPlan:
     """Many images of different sizes, each transformed as `forward` would
-    (one quadrant, one type pair), in one persistent launch."""
+    (one quadrant, one type pair), in one persistent launch; float32 plans
+    also run the batch's adjoint (`adjoint`) the same way."""
 
     def __init__(self, shapes, q: int = Q0, in_dtype: torch.dtype = torch.uint8,
                  acc: torch.dtype = torch.int32):
@@ -330,6 +332,40 @@ class BatchPlan:
         _check(lib.fht_forward_batched(self._plan, ctypes.c_void_p(descs.ctypes.data),
                                        _ptr(ws), _nbytes(ws), _stream(stream)),
                "fht_forward_batched")
+        self._last_ws = ws
+        return outs
+
+    def adjoint(self, grads, outs=None, workspace: torch.Tensor | None = None,
+                stream=None):
+        """Image gradients of the batch (float32 plans): outs[j] = H_j^T
+        grads[j], each as `adjoint(grads[j], h_j, w_j, LAYOUT_QUADRANT, q)`
+        would compute it, in one persistent launch."""
+        if self.acc != torch.float32:
+            raise ValueError("the batched adjoint needs a float32 plan")
+        if len(grads) != len(self.shapes):
+            raise ValueError("one gradient per planned shape")
+        dev = grads[0].device
+        if outs is None:
+            outs = [torch.empty(sh, dtype=torch.float32, device=dev) for sh in self.shapes]
+        rows = []
+        for j, (g, o) in enumerate(zip(grads, outs)):
+            for t, name, want in ((g, f"grads[{j}]", self._out_sizes[j]),
+                                  (o, f"outs[{j}]", self._in_sizes[j])):
+                _dev2d(t, name)
+                if t.dtype != torch.float32:
+                    raise ValueError(f"{name} must be float32")
+                if t.shape != want:
+                    raise ValueError(f"{name}: expected shape {tuple(want)}")
+            rows.append((g.data_ptr(), max(g.stride(0), g.shape[1]),
+                         o.data_ptr(), max(o.stride(0), o.shape[1])))
+        # fht_adjoint_desc is {grad_hough, pitch, grad_img, pitch}, 8 bytes each
+        descs = np.array(rows, dtype=np.int64)
+        ws = self.workspace(dev) if workspace is None else workspace
+        if ws.numel() * ws.element_size() < self.workspace_bytes:
+            raise ValueError("workspace too small")
+        _check(lib.fht_adjoint_batched(self._plan, ctypes.c_void_p(descs.ctypes.data),
+                                       _ptr(ws), _nbytes(ws), _stream(stream)),
+               "fht_adjoint_batched")
         self._last_ws = ws
         return outs
 

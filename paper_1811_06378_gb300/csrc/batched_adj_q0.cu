@@ -1,0 +1,12 @@
+// batched_adj_q0.cu -- one instantiation of the persistent batched kernel:
+// float adjoints of quadrant Q0: slope sign -, image gradient as is
+// (an adjoint runs the opposite sign of its quadrant).
+#include "fht_batched.cuh"
+
+namespace fht {
+namespace batched {
+
+Kernel kernel_adj_q0() { return batched_kernel<kModeAdj, -1>; }
+
+}  // namespace batched
+}  // namespace fht

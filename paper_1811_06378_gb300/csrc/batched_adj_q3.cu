@@ -1,0 +1,12 @@
+// batched_adj_q3.cu -- one instantiation of the persistent batched kernel:
+// float adjoints of quadrant Q3: slope sign -, image gradient transposed
+// (an adjoint runs the opposite sign of its quadrant).
+#include "fht_batched.cuh"
+
+namespace fht {
+namespace batched {
+
+Kernel kernel_adj_q3() { return batched_kernel<kModeAdjT, -1>; }
+
+}  // namespace batched
+}  // namespace fht

@@ -5,7 +5,7 @@
 namespace fht {
 namespace batched {
 
-Kernel kernel_f32_pos() { return batched_forward_kernel<true, 1>; }
+Kernel kernel_f32_pos() { return batched_kernel<kModeF32, 1>; }
 
 }  // namespace batched
 }  // namespace fht

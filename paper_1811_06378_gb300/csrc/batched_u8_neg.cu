@@ -5,7 +5,7 @@
 namespace fht {
 namespace batched {
 
-Kernel kernel_u8_neg() { return batched_forward_kernel<false, -1>; }
+Kernel kernel_u8_neg() { return batched_kernel<kModeU8, -1>; }
 
 }  // namespace batched
 }  // namespace fht

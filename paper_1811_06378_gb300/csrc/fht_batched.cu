@@ -9,6 +9,8 @@
 // running CTA that never waits on a later item, the waits always end. Each
 // wait is still bounded by a clock budget: past it the CTA records
 // FHT_ETIMEOUT and skips the item, so the launch always ends.
+// Float plans carry a second work list, the adjoints (the transpose of every
+// image's quadrant), launched the same way by fht_adjoint_batched.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,48 +25,67 @@
 using namespace fht;
 using namespace fht::batched;
 
-// Direct launches of one plan stage their segment tables in turn in this
-// many pinned tables, so the host can run that many launches ahead.
+// Direct launches of one table stage it in turn in this many pinned copies,
+// so the host can run that many launches ahead.
 constexpr int kDirectTables = 3;
-
-struct fht_plan {
-    int count = 0;
-    int f32 = 0;
-    int sigma = 1;
-    int n_segs = 0, total_items = 0;
-    size_t table_bytes = 0, counters_off = 0, done_off = 0, levels_off = 0;
-    size_t ws_bytes = 0, smem = 0;
-    int n_done = 0;
-    std::vector<int> h, w, rows, cols;   // per image: size, and its quadrant's n x W
-    // pinned staging of the segment table: kDirectTables tables used in turn
-    // by direct launches (each reused only once its previous copy has run),
-    // then one for the latest stream capture
-    void *host_table = nullptr;
-    cudaEvent_t copied[kDirectTables] = {};   // after each direct table's last copy
-    bool copy_pending[kDirectTables] = {};
-    int next_table = 0;
-    long long wait_budget = 4000000000LL;   // ~2 s of SM clocks
-    int dep_bias = 0;
-};
 
 namespace {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
+// One launchable work list (the forward transforms, or the adjoints, of the
+// batch) and its pinned staging. Workspace layout of a launch: the segment
+// table at 0, the counters at counters_off, the per-(image, pass) done
+// counters at done_off, the intermediate levels from levels_off.
+struct Table {
+    int n_segs = 0, total_items = 0, n_done = 0;
+    size_t table_bytes = 0, counters_off = 0, done_off = 0, levels_off = 0;
+    size_t ws_bytes = 0, smem = 0;
+    // kDirectTables copies used in turn by direct launches (each reused only
+    // once its previous copy has run), then one for the latest stream capture
+    void *host_table = nullptr;
+    cudaEvent_t copied[kDirectTables] = {};
+    bool copy_pending[kDirectTables] = {};
+    int next_table = 0;
+};
+
+void release_table(Table &T) {
+    for (int c = 0; c < kDirectTables; ++c) {
+        if (!T.copied[c]) continue;
+        if (T.copy_pending[c]) cudaEventSynchronize(T.copied[c]);
+        cudaEventDestroy(T.copied[c]);
+        T.copied[c] = nullptr;
+    }
+    if (T.host_table) cudaFreeHost(T.host_table);
+    T.host_table = nullptr;
+}
+
 }  // namespace
 
-extern "C" {
+struct fht_plan {
+    int count = 0;
+    int f32 = 0;
+    int q = 0;
+    int sigma = 1;
+    Table fwd, adj;
+    bool has_adj = false;   // float plans also carry the adjoints' table
+    size_t ws_bytes = 0;
+    std::vector<int> h, w, rows, cols;   // per image: size, and its quadrant's n x W
+    long long wait_budget = 4000000000LL;   // ~2 s of SM clocks
+    int dep_bias = 0;
+    size_t last_counters_off = 0;   // counters of the table launched last
+};
 
-fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_quadrant q,
-                                   fht_dtype in_t, fht_dtype acc_t, fht_plan **plan,
-                                   size_t *workspace_bytes) {
-    if (!hs || !ws || !plan || !workspace_bytes || count <= 0 || q < 0 || q > 3)
-        return FHT_EINVAL;
-    const bool f32 = acc_t == FHT_F32 && in_t == FHT_F32;
-    const bool u8 = acc_t == FHT_I32 && in_t == FHT_U8;
-    if (!f32 && !u8) return FHT_EUNSUPPORTED;
+namespace {
+
+// Segments of every image's passes, ordered by pass, variant, m, image.
+// adjoint: the transpose of each image's quadrant (float only), computed
+// as in fht_adjoint: the opposite-sign transform of the gradient with cyclic
+// full-width levels, the final level cropped into the image gradient.
+fht_status build_table(const int *hs, const int *ws, int count, fht_quadrant q, bool f32,
+                       bool adjoint, Table &T) {
+    const bool u8 = !f32;
     std::vector<BatchSeg> segs;
-    std::vector<size_t> level_off;
     size_t level_bytes = 0, smem = 0;
     int n_done = 0;
     struct Pending {
@@ -78,7 +99,9 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
         int K = 0;
         while ((1 << K) < rows) ++K;
         if (K > kMaxBatchK) return FHT_EUNSUPPORTED;
-        const int transpose = q >= 2, sigma = (q == 0 || q == 3) ? 1 : -1;
+        const int transpose = q >= 2;
+        const int sigma_q = (q == 0 || q == 3) ? 1 : -1;
+        const int sigma = adjoint ? -sigma_q : sigma_q;
         const int h_c = transpose ? ws[j] : hs[j], w_c = transpose ? hs[j] : ws[j];
         const int n = rows, W = cols;
         int ms[2], npass;
@@ -90,13 +113,14 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
             ms[1] = K / 2;
             npass = 2;
         }
-        // the one intermediate level (after pass 0), uint16 for uint8 images
+        // the one intermediate level (after pass 0): uint16 for uint8 images;
+        // compact columns for forward transforms, all W (cyclic) for adjoints
         size_t lvl_off = 0;
         int lvl_cols = 0;
         int64_t lvl_pitch = 0;
         const int lvl_type = f32 ? kF32 : kU16;
         if (npass == 2) {
-            lvl_cols = std::min(W, w_c + (1 << ms[0]));
+            lvl_cols = adjoint ? W : std::min(W, w_c + (1 << ms[0]));
             lvl_pitch = (lvl_cols + 63) / 64 * 64;
             lvl_off = level_bytes;
             level_bytes += align256((size_t)n * lvl_pitch * (f32 ? 4 : 2));
@@ -107,17 +131,13 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
             BatchSeg s{};
             PassDesc &d = s.d;
             d.lo_image = p == 0;
-            d.transpose = transpose;
+            d.transpose = adjoint ? 0 : transpose;
             d.hi_final = p == npass - 1;
             d.n = n;
             d.W = W;
             d.K = K;
             d.k0 = k0;
             d.sigma = sigma;
-            d.a_lo = 0;
-            d.a_count = 1 << k0;
-            d.need_lo = 0;
-            d.need_hi = (1 << k1) - 1;
             d.s_count = n >> k1;
             d.t_first = 0;
             d.t_last = n - 1;
@@ -125,12 +145,50 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
             d.row_dir = 1;
             d.shift_win = w_c;
             d.black_wc = w_c;
-            d.lo = p == 0 ? Side{nullptr, 0, f32 ? kF32 : kU8, h_c, w_c}
-                          : Side{nullptr, lvl_pitch, lvl_type, n, lvl_cols};
-            d.hi = d.hi_final ? Side{nullptr, 0, f32 ? kF32 : kI32, 0, W}
+            if (!adjoint) {
+                d.a_lo = 0;
+                d.a_count = 1 << k0;
+                d.need_lo = 0;
+                d.need_hi = (1 << k1) - 1;
+                d.lo = p == 0 ? Side{nullptr, 0, f32 ? kF32 : kU8, h_c, w_c}
                               : Side{nullptr, lvl_pitch, lvl_type, n, lvl_cols};
-            d.p_begin = 0;
-            d.p_count = d.hi.cols;
+                d.hi = d.hi_final ? Side{nullptr, 0, f32 ? kF32 : kI32, 0, W}
+                                  : Side{nullptr, lvl_pitch, lvl_type, n, lvl_cols};
+                d.p_begin = 0;
+                d.p_count = d.hi.cols;
+            } else {
+                // output rows y < h_c of the opposite-sign transform are the
+                // image rows: only the slopes they depend on are computed
+                d.a_lo = 0;
+                d.a_count = ((h_c - 1) >> (K - k0)) + 1;
+                d.need_lo = 0;
+                d.need_hi = (h_c - 1) >> (K - k1);
+                d.cyclic = 1;
+                if (p == 0) {
+                    d.lo = Side{nullptr, 0, kF32, n, W};
+                    d.src_t_first = 0;
+                    d.src_t_last = n - 1;
+                    d.src_row_base = 0;
+                    d.src_row_dir = 1;
+                } else {
+                    d.lo = Side{nullptr, lvl_pitch, kF32, n, W};
+                }
+                if (d.hi_final) {
+                    d.hi = Side{nullptr, 0, kF32, h_c, W};
+                    d.dst_image = 1;
+                    d.dst_h = h_c;
+                    d.dst_w = w_c;
+                    d.dst_transpose = transpose;
+                    d.accumulate = 0;
+                    // only columns X < w_c reach the image: p = X + sigma_plus * n
+                    d.p_begin = sigma > 0 ? n : 0;
+                    d.p_count = w_c;
+                } else {
+                    d.hi = Side{nullptr, lvl_pitch, kF32, n, W};
+                    d.p_begin = 0;
+                    d.p_count = W;
+                }
+            }
             const bool u16_mid = u8 && p == 0;
             if (m >= 4) {
                 const int rb = 1 << (m - 3);
@@ -176,25 +234,146 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
         items += (pd.s.units + pd.s.chunk - 1) / pd.s.chunk;
         segs.push_back(pd.s);
     }
+    T.n_segs = (int)segs.size();
+    T.total_items = items;
+    T.n_done = n_done;
+    T.smem = smem;
+    T.table_bytes = segs.size() * sizeof(BatchSeg);
+    T.counters_off = align256(T.table_bytes);
+    T.done_off = T.counters_off + 256;
+    T.levels_off = align256(T.done_off + (size_t)n_done * sizeof(unsigned int));
+    // intermediate offsets inside the workspace
+    for (auto &s : segs) {
+        s.lo_off += (int64_t)T.levels_off;
+        s.hi_off += (int64_t)T.levels_off;
+    }
+    T.ws_bytes = T.levels_off + level_bytes;
+    if (cudaMallocHost(&T.host_table, (kDirectTables + 1) * T.counters_off) != cudaSuccess) {
+        cudaGetLastError();
+        T.host_table = nullptr;
+        return FHT_ENOMEM;
+    }
+    for (int c = 0; c < kDirectTables; ++c) {
+        if (cudaEventCreateWithFlags(&T.copied[c], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            T.copied[c] = nullptr;
+            return FHT_ECUDA;
+        }
+    }
+    for (int c = 0; c <= kDirectTables; ++c)
+        std::memcpy(static_cast<unsigned char *>(T.host_table) + c * T.counters_off,
+                    segs.data(), T.table_bytes);
+    return FHT_OK;
+}
+
+// Stage table T with the call's pointers (src/dst per image, from the
+// caller's descriptors), copy it and clear the counters on the stream, and
+// launch kernel k over it.
+struct CallPtrs {
+    const void *src;
+    int64_t src_pitch;
+    void *dst;
+    int64_t dst_pitch;
+};
+
+fht_status launch_table(fht_plan *plan, Table &T, const CallPtrs *calls, Kernel k,
+                        const char *name, void *workspace, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FHT_ECUDA;
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    // a direct launch takes the next table of the ring, once the copy of the
+    // launch that used it last has read it
+    const int tab = capturing ? kDirectTables : T.next_table;
+    if (!capturing) {
+        T.next_table = (T.next_table + 1) % kDirectTables;
+        if (T.copy_pending[tab]) {
+            if (cudaEventSynchronize(T.copied[tab]) != cudaSuccess) return FHT_ECUDA;
+            T.copy_pending[tab] = false;
+        }
+    }
+    unsigned char *table = static_cast<unsigned char *>(T.host_table) +
+                           (size_t)tab * T.counters_off;
+    BatchSeg *segs = reinterpret_cast<BatchSeg *>(table);
+    for (int i = 0; i < T.n_segs; ++i) {
+        BatchSeg &sg = segs[i];
+        const CallPtrs &c = calls[sg.image];
+        if (sg.lo_from_image) {
+            sg.d.lo.ptr = const_cast<void *>(c.src);
+            sg.d.lo.pitch = c.src_pitch;
+        } else {
+            sg.d.lo.ptr = ws + sg.lo_off;
+        }
+        if (sg.hi_from_image) {
+            sg.d.hi.ptr = c.dst;
+            sg.d.hi.pitch = c.dst_pitch;
+        } else {
+            sg.d.hi.ptr = ws + sg.hi_off;
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(ws, table, T.counters_off, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !capturing) {
+        e = cudaEventRecord(T.copied[tab], st);
+        if (e == cudaSuccess) T.copy_pending[tab] = true;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ws + T.counters_off, 0, T.levels_off - T.counters_off, st);
+    if (e != cudaSuccess) return FHT_ECUDA;
+    if (T.smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T.smem);
+        if (e != cudaSuccess) return FHT_ECUDA;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarps * 32, T.smem);
+    int grid = std::max(1, sms * std::max(per_sm, 1));
+    grid = std::min(grid, std::max(T.total_items, 1));
+    plan->last_counters_off = T.counters_off;
+    LaunchScope scope(name, st, 0.0);
+    k<<<grid, kWarps * 32, T.smem, st>>>(
+        reinterpret_cast<const BatchSeg *>(ws), T.n_segs, T.total_items,
+        reinterpret_cast<Counters *>(ws + T.counters_off),
+        reinterpret_cast<unsigned int *>(ws + T.done_off), plan->wait_budget, plan->dep_bias);
+    scope.done();
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FHT_OK : FHT_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_quadrant q,
+                                   fht_dtype in_t, fht_dtype acc_t, fht_plan **plan,
+                                   size_t *workspace_bytes) {
+    if (!hs || !ws || !plan || !workspace_bytes || count <= 0 || q < 0 || q > 3)
+        return FHT_EINVAL;
+    const bool f32 = acc_t == FHT_F32 && in_t == FHT_F32;
+    const bool u8 = acc_t == FHT_I32 && in_t == FHT_U8;
+    if (!f32 && !u8) return FHT_EUNSUPPORTED;
+    for (int j = 0; j < count; ++j) {
+        int r = 0, c = 0;
+        if (fht_query_shape(hs[j], ws[j], q, &r, &c) != FHT_OK) return FHT_EINVAL;
+        if (r > (1 << kMaxBatchK)) return FHT_EUNSUPPORTED;
+    }
     fht_plan *P = new (std::nothrow) fht_plan();
     if (!P) return FHT_ENOMEM;
     P->count = count;
     P->f32 = f32;
+    P->q = q;
     P->sigma = (q == 0 || q == 3) ? 1 : -1;
-    P->n_segs = (int)segs.size();
-    P->total_items = items;
-    P->n_done = n_done;
-    P->smem = smem;
-    P->table_bytes = segs.size() * sizeof(BatchSeg);
-    P->counters_off = align256(P->table_bytes);
-    P->done_off = P->counters_off + 256;
-    P->levels_off = align256(P->done_off + (size_t)n_done * sizeof(unsigned int));
-    // intermediate offsets inside the workspace
-    for (auto &s : segs) {
-        s.lo_off += (int64_t)P->levels_off;
-        s.hi_off += (int64_t)P->levels_off;
+    fht_status s = build_table(hs, ws, count, q, f32, false, P->fwd);
+    if (s == FHT_OK && f32) {
+        s = build_table(hs, ws, count, q, true, true, P->adj);
+        P->has_adj = s == FHT_OK;
     }
-    P->ws_bytes = P->levels_off + level_bytes;
+    if (s != FHT_OK) {
+        fht_plan_destroy(P);
+        return s;
+    }
+    P->ws_bytes = std::max(P->fwd.ws_bytes, P->has_adj ? P->adj.ws_bytes : 0);
     for (int j = 0; j < count; ++j) {
         int r = 0, c = 0;
         fht_query_shape(hs[j], ws[j], q, &r, &c);
@@ -203,21 +382,6 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
         P->rows.push_back(r);
         P->cols.push_back(c);
     }
-    if (cudaMallocHost(&P->host_table, (kDirectTables + 1) * P->counters_off) != cudaSuccess) {
-        cudaGetLastError();
-        delete P;
-        return FHT_ENOMEM;
-    }
-    for (int c = 0; c < kDirectTables; ++c) {
-        if (cudaEventCreateWithFlags(&P->copied[c], cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            fht_plan_destroy(P);
-            return FHT_ECUDA;
-        }
-    }
-    for (int c = 0; c <= kDirectTables; ++c)
-        std::memcpy(static_cast<unsigned char *>(P->host_table) + c * P->counters_off,
-                    segs.data(), P->table_bytes);
     *plan = P;
     *workspace_bytes = P->ws_bytes;
     return FHT_OK;
@@ -227,75 +391,37 @@ fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void
                                size_t workspace_bytes, void *stream) {
     if (!plan || !descs || !workspace || workspace_bytes < plan->ws_bytes) return FHT_EINVAL;
     if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return FHT_EINVAL;
+    std::vector<CallPtrs> calls(plan->count);
     for (int j = 0; j < plan->count; ++j) {
         const fht_image_desc &dj = descs[j];
         if (!dj.img || !dj.out || dj.img_pitch < plan->w[j] || dj.out_pitch < plan->cols[j])
             return FHT_EINVAL;
+        calls[j] = CallPtrs{dj.img, dj.img_pitch, dj.out, dj.out_pitch};
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    unsigned char *ws = static_cast<unsigned char *>(workspace);
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FHT_ECUDA;
-    const bool capturing = cs != cudaStreamCaptureStatusNone;
-    // a direct launch takes the next table of the ring, once the copy of the
-    // launch that used it last has read it
-    const int tab = capturing ? kDirectTables : plan->next_table;
-    if (!capturing) {
-        plan->next_table = (plan->next_table + 1) % kDirectTables;
-        if (plan->copy_pending[tab]) {
-            if (cudaEventSynchronize(plan->copied[tab]) != cudaSuccess) return FHT_ECUDA;
-            plan->copy_pending[tab] = false;
-        }
-    }
-    unsigned char *table = static_cast<unsigned char *>(plan->host_table) +
-                           (size_t)tab * plan->counters_off;
-    BatchSeg *segs = reinterpret_cast<BatchSeg *>(table);
-    for (int i = 0; i < plan->n_segs; ++i) {
-        BatchSeg &sg = segs[i];
-        const fht_image_desc &im = descs[sg.image];
-        if (sg.lo_from_image) {
-            sg.d.lo.ptr = const_cast<void *>(im.img);
-            sg.d.lo.pitch = im.img_pitch;
-        } else {
-            sg.d.lo.ptr = ws + sg.lo_off;
-        }
-        if (sg.hi_from_image) {
-            sg.d.hi.ptr = im.out;
-            sg.d.hi.pitch = im.out_pitch;
-        } else {
-            sg.d.hi.ptr = ws + sg.hi_off;
-        }
-    }
-    cudaError_t e = cudaMemcpyAsync(ws, table, plan->counters_off, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !capturing) {
-        e = cudaEventRecord(plan->copied[tab], st);
-        if (e == cudaSuccess) plan->copy_pending[tab] = true;
-    }
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(ws + plan->counters_off, 0,
-                            plan->levels_off - plan->counters_off, st);
-    if (e != cudaSuccess) return FHT_ECUDA;
     const Kernel k = plan->f32 ? (plan->sigma > 0 ? kernel_f32_pos() : kernel_f32_neg())
                                : (plan->sigma > 0 ? kernel_u8_pos() : kernel_u8_neg());
-    if (plan->smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
-        if (e != cudaSuccess) return FHT_ECUDA;
+    return launch_table(plan, plan->fwd, calls.data(), k,
+                        plan->f32 ? "batched_forward_f32" : "batched_forward_u8_i32", workspace,
+                        stream);
+}
+
+fht_status fht_adjoint_batched(fht_plan *plan, const fht_adjoint_desc *descs, void *workspace,
+                               size_t workspace_bytes, void *stream) {
+    if (!plan || !descs || !workspace || workspace_bytes < plan->ws_bytes) return FHT_EINVAL;
+    if (!plan->has_adj) return FHT_EUNSUPPORTED;
+    if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return FHT_EINVAL;
+    std::vector<CallPtrs> calls(plan->count);
+    for (int j = 0; j < plan->count; ++j) {
+        const fht_adjoint_desc &dj = descs[j];
+        if (!dj.grad_hough || !dj.grad_img || dj.grad_hough_pitch < plan->cols[j] ||
+            dj.grad_img_pitch < plan->w[j])
+            return FHT_EINVAL;
+        calls[j] = CallPtrs{dj.grad_hough, dj.grad_hough_pitch, dj.grad_img, dj.grad_img_pitch};
     }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarps * 32, plan->smem);
-    int grid = std::max(1, sms * std::max(per_sm, 1));
-    grid = std::min(grid, std::max(plan->total_items, 1));
-    LaunchScope scope(plan->f32 ? "batched_forward_f32" : "batched_forward_u8_i32", st, 0.0);
-    k<<<grid, kWarps * 32, plan->smem, st>>>(
-        reinterpret_cast<const BatchSeg *>(ws), plan->n_segs, plan->total_items,
-        reinterpret_cast<Counters *>(ws + plan->counters_off),
-        reinterpret_cast<unsigned int *>(ws + plan->done_off), plan->wait_budget,
-        plan->dep_bias);
-    scope.done();
-    e = cudaGetLastError();
-    return e == cudaSuccess ? FHT_OK : FHT_ECUDA;
+    const Kernel k = plan->q == 0 ? kernel_adj_q0() : plan->q == 1 ? kernel_adj_q1()
+                   : plan->q == 2 ? kernel_adj_q2() : kernel_adj_q3();
+    return launch_table(plan, plan->adj, calls.data(), k, "batched_adjoint_f32", workspace,
+                        stream);
 }
 
 fht_status fht_batched_status(const fht_plan *plan, const void *workspace, void *stream) {
@@ -303,7 +429,7 @@ fht_status fht_batched_status(const fht_plan *plan, const void *workspace, void 
     int err = 0;
     const unsigned char *ws = static_cast<const unsigned char *>(workspace);
     cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(&err, ws + plan->counters_off + offsetof(Counters, error), sizeof(int),
+    if (cudaMemcpyAsync(&err, ws + plan->last_counters_off + offsetof(Counters, error), sizeof(int),
                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return FHT_ECUDA;
@@ -319,12 +445,8 @@ fht_status fht_batched_test_hooks(fht_plan *plan, long long wait_budget_cycles, 
 
 void fht_plan_destroy(fht_plan *plan) {
     if (!plan) return;
-    for (int c = 0; c < kDirectTables; ++c) {
-        if (!plan->copied[c]) continue;
-        if (plan->copy_pending[c]) cudaEventSynchronize(plan->copied[c]);
-        cudaEventDestroy(plan->copied[c]);
-    }
-    if (plan->host_table) cudaFreeHost(plan->host_table);
+    release_table(plan->fwd);
+    release_table(plan->adj);
     delete plan;
 }
 

@@ -1,7 +1,8 @@
-// fht_batched.cuh -- the persistent batched-forward kernel: segment table
-// layout, dependency counters and the item loop. Each (type, sign)
-// instantiation lives in its own translation unit (batched_*.cu) so that
-// they compile in parallel; fht_batched.cu holds the host-side plan.
+// fht_batched.cuh -- the persistent batched kernel (forward transforms and
+// FP32 adjoints of many images of different sizes): segment table layout,
+// dependency counters and the item loop. Each (mode, sign) instantiation
+// lives in its own translation unit (batched_*.cu) so that they compile in
+// parallel; fht_batched.cu holds the host-side plan.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,6 +27,11 @@ constexpr int kUnitsPerItem = FHT_BATCH_UNITS;
 // Kernel variants. uint8 -> int32: single-pass images, first passes into a
 // uint16 level, and int32 final passes from it. float: one variant per M.
 enum : int { kVarU8Final = 0, kVarU8Level = 10, kVarU16Final = 20, kVarF32 = 30 };
+
+// What one launch runs: uint8 -> int32 forward transforms, float forward
+// transforms, or float adjoints whose final level goes to the image gradient
+// as is (quadrants Q0, Q1) or transposed (Q2, Q3).
+enum : int { kModeU8 = 0, kModeF32 = 1, kModeAdj = 2, kModeAdjT = 3 };
 
 struct BatchSeg {
     PassDesc d;          // complete; lo/hi pointers and pitches written by the host per call
@@ -53,28 +59,30 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     return v;
 }
 
-template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
+template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __device__ __forceinline__ void run_item(const PassDesc &d, int gy, int tile, unsigned char *sm) {
-    fused_forward_item<MA, MB, SG, false, FIN, Acc, SrcE, MidE, DstE>(
+    fused_forward_item<MA, MB, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(
         d, gy, tile, reinterpret_cast<MidE *>(sm));
 }
 
-template <int SG, int FIN, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int SG, int FIN, typename Acc, typename SrcE, typename MidE, typename DstE,
+          bool ADJ = false>
 __device__ __forceinline__ void run_item_m(int m, const PassDesc &d, int gy, int tile,
                                            unsigned char *sm) {
     switch (m) {
-    case 0: run_item<0, 0, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 1: run_item<1, 0, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 2: run_item<2, 0, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 3: run_item<3, 0, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 4: run_item<3, 1, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 5: run_item<3, 2, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    default: run_item<3, 3, SG, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 0: run_item<0, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 1: run_item<1, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 2: run_item<2, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 3: run_item<3, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 4: run_item<3, 1, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 5: run_item<3, 2, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    default: run_item<3, 3, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
     }
 }
 
-// one batch = one quadrant, so one sign: the kernel is instantiated per sign.
+// one batch = one quadrant, so one sign: the kernel is instantiated per mode
+// and sign (an adjoint's sign is the opposite of its quadrant's).
 // Thread 0 claims the next item while the CTA works on the current one (the
 // claim's latency is hidden), finds its segment and waits for its dependency;
 // all threads then copy the segment's pass descriptor (complete, pointers
@@ -84,10 +92,10 @@ __device__ __forceinline__ void run_item_m(int m, const PassDesc &d, int gy, int
 // Holding one claimed item ahead keeps the waits finite: the smallest
 // unfinished item is always some CTA's current item, and everything it
 // depends on has a smaller index.
-template <bool F32, int SG>
+template <int MODE, int SG>
 __global__ void __launch_bounds__(kWarps * 32, 2)
-    batched_forward_kernel(const BatchSeg *segs, int n_segs, int total_items, Counters *ctr,
-                           unsigned int *done, long long wait_budget, int dep_bias) {
+    batched_kernel(const BatchSeg *segs, int n_segs, int total_items, Counters *ctr,
+                   unsigned int *done, long long wait_budget, int dep_bias) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item, s_skip, s_m, s_variant, s_tiles, s_first, s_done, s_units, s_chunk;
     __shared__ int s_seg;
@@ -157,7 +165,15 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
             for (int u = u0; u < u1; ++u) {
                 if (u > u0) __syncthreads();   // the previous unit's reads of the shared tile
                 const int gy = u / tiles, tile = u - gy * tiles;
-                if constexpr (F32) {
+                if constexpr (MODE == kModeAdj || MODE == kModeAdjT) {
+                    // float adjoint: cyclic intermediate levels, image gradient last
+                    if (d.hi_final)
+                        run_item_m<SG, MODE == kModeAdjT ? 2 : 1, float, float, float, float,
+                                   true>(m, d, gy, tile, smem_raw);
+                    else
+                        run_item_m<SG, 0, float, float, float, float, true>(m, d, gy, tile,
+                                                                            smem_raw);
+                } else if constexpr (MODE == kModeF32) {
                     if (d.hi_final)
                         run_item_m<SG, 1, float, float, float, float>(m, d, gy, tile, smem_raw);
                     else
@@ -192,11 +208,17 @@ __global__ void __launch_bounds__(kWarps * 32, 2)
 
 using Kernel = void (*)(const BatchSeg *, int, int, Counters *, unsigned int *, long long, int);
 
-// The four instantiations, one per translation unit.
+// The instantiations, one per translation unit: forward transforms per type
+// and sign; adjoints per quadrant (sign, and whether the image gradient is
+// transposed).
 Kernel kernel_f32_pos();
 Kernel kernel_f32_neg();
 Kernel kernel_u8_pos();
 Kernel kernel_u8_neg();
+Kernel kernel_adj_q0();
+Kernel kernel_adj_q1();
+Kernel kernel_adj_q2();
+Kernel kernel_adj_q3();
 
 }  // namespace batched
 }  // namespace fht

@@ -133,3 +133,76 @@ def test_batched_graph_keeps_captured_descriptors(fht):
         assert torch.equal(o, fht.forward(x, 0))
     for x, o in zip(b, ob):
         assert torch.equal(o, fht.forward(x, 0))
+
+
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
+def test_batched_adjoint_matches_per_image_and_oracle(fht, q):
+    """fht_adjoint_batched over mixed sizes (one- and two-pass images,
+    ragged sides, a 1 x 1 image) equals fht_adjoint per image bit for bit,
+    and the oracle's FP32 transpose on sampled images; a forward call on the
+    same plan and workspace in between leaves it unchanged."""
+    shapes = _mixed_shapes()
+    plan = fht.BatchPlan(shapes, q, torch.float32, torch.float32)
+    rng = np.random.default_rng(40 + q)
+    grads = [torch.from_numpy(rng.standard_normal(sh).astype(np.float32)).cuda()
+             for sh in plan.out_shapes]
+    ws = plan.workspace("cuda")
+    outs = plan.adjoint(grads, workspace=ws)
+    assert plan.status(ws) == 0
+    imgs = [torch.from_numpy(random_image(h, w, "f32", seed=h + w)).cuda() for h, w in shapes]
+    plan.forward(imgs, workspace=ws)
+    again = plan.adjoint(grads, workspace=ws)
+    assert plan.status(ws) == 0
+    for (h, w), g, o, o2 in zip(shapes, grads, outs, again):
+        want = fht.adjoint(g, h, w, fht.LAYOUT_QUADRANT, q)
+        assert torch.equal(o, want), (h, w)
+        assert torch.equal(o2, want), (h, w)
+    for j in (0, 3, 5, 6):
+        h, w = shapes[j]
+        want = O.adjoint_quadrant(grads[j].cpu().numpy(), h, w, q, "f32")
+        assert (outs[j].cpu().numpy() == want).all(), shapes[j]
+
+
+def test_batched_adjoint_is_transpose_of_batched_forward(fht):
+    """<H x, g> = <x, H^T g> per image, both sides from the batched calls
+    (FP64 sums of FP32 results, within the FP32 bound 1e-5 * sum|terms|)."""
+    shapes = batch_shapes(64, seed=5)
+    plan = fht.BatchPlan(shapes, 2, torch.float32, torch.float32)
+    rng = np.random.default_rng(11)
+    xs = [torch.from_numpy(rng.standard_normal(sh).astype(np.float32)).cuda() for sh in shapes]
+    gs = [torch.from_numpy(rng.standard_normal(sh).astype(np.float32)).cuda()
+          for sh in plan.out_shapes]
+    ws = plan.workspace("cuda")
+    hx = plan.forward(xs, workspace=ws)
+    htg = plan.adjoint(gs, workspace=ws)
+    for x, g, a, b in zip(xs, gs, hx, htg):
+        lhs = float((a.double() * g.double()).sum())
+        rhs = float((x.double() * b.double()).sum())
+        scale = float((a.double().abs() * g.double().abs()).sum())
+        assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def test_batched_adjoint_graph_replay(fht):
+    """The batched adjoint captured in a CUDA graph replays the captured
+    descriptors."""
+    shapes = [(200, 300), (129, 64), (40, 1000)]
+    plan = fht.BatchPlan(shapes, 1, torch.float32, torch.float32)
+    rng = np.random.default_rng(3)
+    gs = [torch.from_numpy(rng.standard_normal(sh).astype(np.float32)).cuda()
+          for sh in plan.out_shapes]
+    ws = plan.workspace("cuda")
+    outs = [torch.empty(sh, dtype=torch.float32, device="cuda") for sh in shapes]
+    plan.adjoint(gs, outs, ws)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.adjoint(gs, outs, ws, stream=s)
+    for o in outs:
+        o.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert plan.status(ws) == 0
+    for (h, w), gr, o in zip(shapes, gs, outs):
+        assert torch.equal(o, fht.adjoint(gr, h, w, fht.LAYOUT_QUADRANT, 1))
