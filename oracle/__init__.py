@@ -36,6 +36,11 @@ with gcc, no fast-math). Readings of points the paper leaves open:
 6. fhtshift rotates row t of a quadrant right by floor(b/2) (+ t for the
    positive-sign quadrants), b = W - w_in - t the black-zone width.
 7. Angle ranges map to slopes by t = (n-1)*tan(theta); see ``angle_to_slopes``.
+8. The shear of Section 4 (``sheared_quadrant``): row y of the (transposed)
+   image is shifted cyclically right by s(y) = floor(y*spl + 1/2) columns
+   (spl = "shift per line"; the paper gives no rounding), then the plain
+   quadrant transform runs on the cyclic width W = w + n, which the paper
+   keeps ("the black zone will simply move").
 """
 
 from __future__ import annotations
@@ -327,6 +332,69 @@ def angle_to_slopes(phi_lo: float, phi_hi: float, h: int, w: int
         if lo[q] > hi[q]:
             lo[q] = hi[q] = -1
     return lo, hi
+
+
+# ---------------------------------------------------------------- shear (Section 4)
+
+def shear_shifts(rows: int, spl: float) -> np.ndarray:
+    """s(y) = floor(y*spl + 1/2) for y < rows: the shift per line of Section 4
+    rounded half up, the product and the sum each rounded to float64 (no fused
+    multiply-add), so that an integer decision taken from the same double
+    arithmetic elsewhere agrees."""
+    y = np.arange(rows, dtype=np.float64)
+    prod = y * np.float64(spl)
+    return np.floor(prod + np.float64(0.5)).astype(np.int64)
+
+
+def sheared_quadrant(img: np.ndarray, q: int, spl: float, kind: str = "i64",
+                     t_lo: int = 0, t_hi: int | None = None) -> np.ndarray:
+    """Quadrant q of the sheared image (Section 4): row y of the image (of the
+    transposed image for Q2/Q3) is zero-padded to the cyclic width W = w + n
+    and rotated right by s(y) columns; the plain butterfly of that n x W array
+    with the quadrant's sign, rows t_lo..t_hi. A line with dx/dy = k in the
+    image (columns per row of the transposed image for Q2/Q3) lies on the
+    sheared image's slope k + spl: with spl = tan(beta) the quadrant's slopes
+    t/(n-1) in [0, 1] cover k in [-spl, 1 - spl]."""
+    src = img.T if TRANSPOSED[q] else img
+    n, W = quadrant_geometry(img.shape[0], img.shape[1], q)
+    P = padded(src, n, W, kind)
+    s = shear_shifts(src.shape[0], spl)
+    for y in range(src.shape[0]):
+        P[y] = np.roll(P[y], int(s[y]))
+    H = butterfly(P, SIGMA[q], kind)
+    t_hi = n - 1 if t_hi is None else t_hi
+    return H[t_lo:t_hi + 1].copy()
+
+
+def shear_range(phi_lo: float, phi_hi: float, h: int, w: int
+                ) -> tuple[int, float, int, int]:
+    """One sheared quadrant for the line angles [phi_lo, phi_hi] (degrees,
+    the quadrant spans of ``angle_to_slopes``): (q, spl, t_lo, t_hi), or
+    None when the range does not fit one quadrant.
+
+    Mostly vertical ranges (inside [-45, 45]) use Q0 with spl = tan(phi_hi):
+    its row t then holds the lines at phi(t) = atan(spl - t/(n-1)), from phi_hi
+    at t = 0 down to phi_lo. Mostly horizontal ranges (inside [45, 135]) use Q3
+    with spl = -tan(phi_lo - 90): phi(t) = 90 + atan(t/(n-1) - spl), from phi_lo
+    up. t runs from 0 to floor((n-1) * (tan(b) - tan(a))), a and b the range's
+    ends measured from the quadrant's axis, which must differ by at most 1 in
+    tangent (45 degrees around the axis)."""
+    if phi_lo > phi_hi:
+        return None
+    if -45.0 <= phi_lo and phi_hi <= 45.0:
+        q, a, b = Q0, phi_lo, phi_hi
+        spl = math.tan(math.radians(b))
+    elif 45.0 <= phi_lo and phi_hi <= 135.0:
+        q, a, b = Q3, phi_lo - 90.0, phi_hi - 90.0
+        spl = -math.tan(math.radians(a))
+    else:
+        return None
+    span = math.tan(math.radians(b)) - math.tan(math.radians(a))
+    if span > 1.0 + 1e-12:
+        return None
+    n, _ = quadrant_geometry(h, w, q)
+    t_hi = 0 if n == 1 else min(n - 1, math.floor((n - 1) * span + 1e-9))
+    return q, spl, 0, t_hi
 
 
 # ---------------------------------------------------------------- adjoints

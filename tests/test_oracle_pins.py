@@ -416,3 +416,107 @@ def test_sampled_points_match_full_transform():
         ts = rng.integers(0, n2, 50)
         xs = rng.integers(0, W2, 50)
         assert (O.points(img, q, ts, xs, full_layout=True) == F[ts, xs]).all()
+
+
+# --------------------------------------------------------------- shear (Section 4)
+
+def test_shear_shifts_round_half_up():
+    """s(y) = floor(y*spl + 1/2): exact halves round up, negative shifts round
+    towards +infinity at halves, spl = 0 gives no shift."""
+    assert list(O.shear_shifts(5, 0.5)) == [0, 1, 1, 2, 2]
+    assert list(O.shear_shifts(5, -0.5)) == [0, 0, -1, -1, -2]
+    assert list(O.shear_shifts(4, 0.0)) == [0, 0, 0, 0]
+    assert list(O.shear_shifts(4, 1.0)) == [0, 1, 2, 3]
+    assert list(O.shear_shifts(4, -1.0)) == [0, -1, -2, -3]
+
+
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
+def test_shear_zero_is_the_plain_quadrant(q):
+    img = random_image(37, 21, "u8", seed=q)
+    assert (O.sheared_quadrant(img, q, 0.0) == O.quadrant(img, q)).all()
+
+
+@pytest.mark.parametrize("q,spl", [(0, 0.37), (1, -0.6), (2, 1.0), (3, -1.0), (0, -0.25),
+                                   (3, 0.8)])
+def test_shear_equals_brute_force_sums(q, spl):
+    """Every point is the sum of the image along the pattern minus the per-row
+    shift, H[t][x] = sum_y P[y][(x + sigma*off(t, y) - s(y)) mod W], written
+    out with the closed-form offsets (no butterfly, no array rotation)."""
+    img = random_image(11, 6, "u8", seed=7)
+    h, w = img.shape
+    src = img.T if O.TRANSPOSED[q] else img
+    n, W = O.quadrant_geometry(h, w, q)
+    sg = O.SIGMA[q]
+    s = [math.floor(y * spl + 0.5) for y in range(src.shape[0])]
+    H = np.zeros((n, W), np.int64)
+    for t in range(n):
+        for x in range(W):
+            acc = 0
+            for y in range(src.shape[0]):
+                c = (x + sg * O.offset(n, t, y) - s[y]) % W
+                if c < src.shape[1]:
+                    acc += int(src[y, c])
+            H[t, x] = acc
+    assert (O.sheared_quadrant(img, q, spl) == H).all()
+
+
+def test_unit_shear_turns_45_degree_row_into_column_sums():
+    """off_n(n-1, y) = y, so the 45-degree row after a unit shear against it
+    sums straight down the columns: Q0 with spl = 1 and Q1 with spl = -1 give
+    the image's column sums at their row n - 1 (and Q3 with spl = 1 the row
+    sums, through the transpose)."""
+    img = random_image(29, 40, "u8", seed=3)
+    h, w = img.shape
+    n, W = O.quadrant_geometry(h, w, 0)
+    col = np.zeros(W, np.int64)
+    col[:w] = img.astype(np.int64).sum(axis=0)
+    assert (O.sheared_quadrant(img, 0, 1.0)[n - 1] == col).all()
+    assert (O.sheared_quadrant(img, 1, -1.0)[n - 1] == col).all()
+    n3, W3 = O.quadrant_geometry(h, w, 3)
+    row = np.zeros(W3, np.int64)
+    row[:h] = img.astype(np.int64).sum(axis=1)
+    assert (O.sheared_quadrant(img, 3, 1.0)[n3 - 1] == row).all()
+
+
+@pytest.mark.parametrize("phi", [-14.0, -6.5, 0.0, 3.0, 11.0, 15.0])
+def test_sheared_range_finds_lines_at_their_angle(phi):
+    """A straight line at angle phi (dx/dy = -tan(phi), the angle convention
+    of the quadrants: Q0 holds [-45, 0]) rasterised into a 256 x 256 image
+    peaks, in the one sheared quadrant that shear_range picks for
+    [-15, 15] degrees, at the row whose angle is phi within one slope step, and
+    the range's rows stop exactly at its ends."""
+    n = 256
+    q, spl, t_lo, t_hi = O.shear_range(-15.0, 15.0, n, n)
+    assert q == 0 and t_lo == 0
+    assert spl == pytest.approx(math.tan(math.radians(15.0)))
+    # row angles: phi(t) = atan(spl - t/(n-1)) within [-15, 15], the next outside
+    ang = lambda t: math.degrees(math.atan(spl - t / (n - 1)))  # noqa: E731
+    assert ang(0) == pytest.approx(15.0)
+    assert ang(t_hi) >= -15.0 - 1e-9 and ang(t_hi + 1) < -15.0
+    img = np.zeros((n, n), np.uint8)
+    k = -math.tan(math.radians(phi))
+    x0 = n / 2 - k * n / 2
+    for y in range(n):
+        img[y, int(math.floor(x0 + k * y + 0.5))] = 1
+    H = O.sheared_quadrant(img, q, spl, t_lo=t_lo, t_hi=t_hi)
+    t_pk = int(np.unravel_index(np.argmax(H), H.shape)[0])
+    step = math.degrees(math.atan(1 / (n - 1)))
+    assert abs(ang(t_pk) - phi) <= 1.5 * step
+    # the pattern (within log2(n)/6 columns of straight), the shear's and the
+    # line's roundings (half a column each) leave at most about 2.3 columns
+    # between the peak's pattern and the line: most of its pixels are summed
+    assert H.max() >= 0.5 * n
+
+
+def test_shear_range_horizontal_and_rejections():
+    """Mostly horizontal ranges go to Q3 (angles from phi_lo up); ranges that
+    cross 45 degrees or span more than 45 degrees around an axis do not fit
+    one quadrant."""
+    q, spl, t_lo, t_hi = O.shear_range(75.0, 105.0, 300, 2048)
+    n, _ = O.quadrant_geometry(300, 2048, 3)
+    assert q == 3 and t_lo == 0
+    assert spl == pytest.approx(math.tan(math.radians(15.0)))
+    assert t_hi == math.floor((n - 1) * 2 * math.tan(math.radians(15.0)) + 1e-9)
+    assert O.shear_range(30.0, 60.0, 64, 64) is None
+    assert O.shear_range(-30.0, 30.0, 64, 64) is None
+    assert O.shear_range(-45.0, 0.0, 64, 64)[3] == 63
