@@ -122,6 +122,9 @@ struct QuadPlan {
     int lvl_cols[5];
     int64_t lvl_pitch[5];
     size_t buf_bytes[2];
+    // adjoint: the level the final pass reads is windowed when win_len > 0
+    // (PassDesc::lo_win / hi_win)
+    int win_len, win_c;
 };
 
 // Plan of quadrant q. With `adjoint`, the plan is the transform's transpose:
@@ -152,6 +155,9 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
     P.k[0] = 0;
     for (int p = 0; p < P.npass; ++p) P.k[p + 1] = P.k[p] + P.m[p];
     P.buf_bytes[0] = P.buf_bytes[1] = 0;
+    P.win_len = P.win_c = 0;
+    if (adjoint && P.npass >= 2)
+        adjoint_window(P.w_c, P.W, P.K, P.m[P.npass - 1], P.sigma, &P.win_len, &P.win_c);
     for (int p = 1; p < P.npass; ++p) {
         int k = P.k[p];
         int type = acc_elem;
@@ -160,6 +166,11 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
         P.lvl_type[p] = type;
         P.lvl_cols[p] = adjoint ? P.W : std::min(P.W, P.w_c + (1 << k));
         P.lvl_pitch[p] = (int64_t)align_up(P.lvl_cols[p], 64);
+        if (P.win_len > 0 && p == P.npass - 1) {
+            // windowed: loads of 8 from any index below win_len stay in the row
+            P.lvl_cols[p] = P.win_len;
+            P.lvl_pitch[p] = (int64_t)align_up((size_t)P.win_len + 16, 64);
+        }
         size_t bytes = align_up((size_t)P.n * P.lvl_pitch[p] * elem_bytes(type), 256);
         size_t &slot = P.buf_bytes[(p - 1) % 2];
         slot = std::max(slot, bytes);
@@ -362,6 +373,17 @@ fht_status run_adjoint(const QuadPlan &P, const Side &grad_img, const Side &grad
             d.src_t_last = fm.t_last;
             d.src_row_base = fm.row_base;
             d.src_row_dir = fm.row_dir;
+        }
+        d.win_len = P.win_len;
+        d.win_c = P.win_c;
+        if (P.win_len > 0) {
+            d.lo_win = p == P.npass - 1;
+            d.hi_win = p == P.npass - 2;
+            if (d.hi_win) {
+                // the pass still covers every column; its stores keep the windows
+                d.hi.cols = P.W;
+                d.p_count = P.W;
+            }
         }
         if (d.hi_final) {
             d.dst_image = 1;

@@ -119,9 +119,18 @@ fht_status build_table(const int *hs, const int *ws, int count, fht_quadrant q, 
         int lvl_cols = 0;
         int64_t lvl_pitch = 0;
         const int lvl_type = f32 ? kF32 : kU16;
+        int win_len = 0, win_c = 0;
         if (npass == 2) {
             lvl_cols = adjoint ? W : std::min(W, w_c + (1 << ms[0]));
             lvl_pitch = (lvl_cols + 63) / 64 * 64;
+            if (adjoint) {
+                // the level the final pass reads keeps each row's window only
+                adjoint_window(w_c, W, K, ms[1], sigma, &win_len, &win_c);
+                if (win_len > 0) {
+                    lvl_cols = win_len;
+                    lvl_pitch = (win_len + 16 + 63) / 64 * 64;
+                }
+            }
             lvl_off = level_bytes;
             level_bytes += align256((size_t)n * lvl_pitch * (f32 ? 4 : 2));
         }
@@ -164,6 +173,10 @@ fht_status build_table(const int *hs, const int *ws, int count, fht_quadrant q, 
                 d.need_lo = 0;
                 d.need_hi = (h_c - 1) >> (K - k1);
                 d.cyclic = 1;
+                d.win_len = win_len;
+                d.win_c = win_c;
+                d.lo_win = win_len > 0 && p == 1;
+                d.hi_win = win_len > 0 && p == 0;
                 if (p == 0) {
                     d.lo = Side{nullptr, 0, kF32, n, W};
                     d.src_t_first = 0;
@@ -171,7 +184,7 @@ fht_status build_table(const int *hs, const int *ws, int count, fht_quadrant q, 
                     d.src_row_base = 0;
                     d.src_row_dir = 1;
                 } else {
-                    d.lo = Side{nullptr, lvl_pitch, kF32, n, W};
+                    d.lo = Side{nullptr, lvl_pitch, kF32, n, lvl_cols};
                 }
                 if (d.hi_final) {
                     d.hi = Side{nullptr, 0, kF32, h_c, W};

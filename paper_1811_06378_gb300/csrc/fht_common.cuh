@@ -76,11 +76,40 @@ struct PassDesc {
     int t_first, t_last, row_base, row_dir;
     // final level only: fhtshift rotation fused into the row mapping
     int shift_on, shift_win, shift_inverse;
+    // Windowed adjoint level: the final pass of an adjoint reads each row of
+    // the level before it only on the win_len columns that reach the cropped
+    // image gradient, so that level keeps just those. Row (strip s, slope a)
+    // holds the columns x of its window, based at win_base(d, s, a), at
+    // j = (x - base) mod W < win_len; its pitch is >= win_len + 8. hi_win:
+    // this pass writes such a level; lo_win: it reads one.
+    int lo_win, hi_win, win_len, win_c;
 };
 
 __host__ __device__ inline int64_t floor_mod(int64_t v, int64_t m) {
     int64_t r = v % m;
     return r < 0 ? r + m : r;
+}
+
+// v mod W for v in (-2W, 2W); other values take the general remainder.
+__host__ __device__ inline int wrap_w(int v, int W) {
+    if (v < 0) v += W;
+    if (v >= W) v -= W;
+    if ((unsigned)v >= (unsigned)W) {
+        v %= W;
+        if (v < 0) v += W;
+    }
+    return v;
+}
+
+// First column of the window of level row (strip s, slope a): the final
+// pass's group a reads row s sheared by sigma*a*s from column
+// win_c + sigma*a*s on, so the window moves with the shear. It starts 8 to 15
+// columns before that column, on a multiple of 8: a lane's 8 columns that
+// hold any needed column then start inside the window (no wrap), and
+// aligned rows stay aligned.
+__host__ __device__ inline int win_base(const PassDesc &d, int s, int a) {
+    const int b = wrap_w(d.win_c + d.sigma * a * s - 8, d.W);
+    return b & ~7;
 }
 
 // fhtshift rotation of slope row t (Section 5): the w_in + t meaningful

@@ -399,6 +399,29 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
                                              int A_off, int wbase, int i0, Acc (&v)[RA][kV]) {
     constexpr int sg = SG;
     const int splus = sg > 0 ? 1 : 0;
+    if constexpr (ADJ) {
+        if (!d.lo_image && d.lo_win) {
+            // windowed level: row s0 + r of group a at its stored index; the
+            // 8 columns never wrap inside a window (win_len <= W - 16), and
+            // columns outside it feed no stored output, so any in-bounds
+            // index (0) serves for them
+            const SrcE *base = reinterpret_cast<const SrcE *>(d.lo.ptr);
+            const int64_t stride = d.lo.pitch << d.k0;
+            const SrcE *p0 = base + ((((int64_t)S << M) + s0) << d.k0) * d.lo.pitch +
+                             (int64_t)a * d.lo.pitch;
+#pragma unroll
+            for (int r = 0; r < RA; ++r) {
+                const int sp = s0 + r;
+                const int p_first = A_off + sg * (i0 + a * sp);
+                const int lo = sg > 0 ? p_first : p_first - (kV - 1);
+                int j = wrap_w(lo - win_base(d, (S << M) + sp, a), d.W);
+                if (j >= d.win_len) j = 0;
+                load8_fast<SrcE, Acc>(p0 + r * stride, j, v[r]);
+                if constexpr (sg < 0) reverse8(v[r]);
+            }
+            return;
+        }
+    }
     // ascending source-column range [lo_min, hi_max) over the warp item
     int lo_min, hi_max;
     if (sg > 0) {
@@ -571,6 +594,73 @@ __device__ __forceinline__ void store_rows(const PassDesc &d, const DestCols &c,
         }
     }
     }
+}
+
+// One row of a windowed adjoint level where the lane's 8 columns do not land
+// as one run inside the window: each column x < W goes to j = (x - b) mod W
+// if j < L.
+template <typename Acc, typename DstE>
+__device__ __noinline__ void store_win_edge(DstE *row, int lo, int b, int W, int L, Vec8<Acc> v) {
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        const int x = lo + k;
+        if (x >= W) continue;
+        int j = x - b;
+        if (j < 0) j += W;
+        if (j < L) row[j] = (DstE)v.x[k];
+    }
+}
+
+// R consecutive rows hi_r0.. of a windowed adjoint level (written by the pass
+// before an adjoint's final pass, levels k1): this lane's 8 ascending
+// columns lo.. go to each row's window only.
+template <int SG, int R, typename Acc, typename DstE>
+__device__ __forceinline__ void store_rows_win(const PassDesc &d, int k1, int lo, int hi_r0,
+                                               const Acc (&v)[R][kV]) {
+    const int W = d.W, L = d.win_len;
+    if (lo >= W) return;   // past the level's last column
+    DstE *base = reinterpret_cast<DstE *>(d.hi.ptr);
+    const int mask = (1 << k1) - 1;
+    const bool whole = lo + kV <= W;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = hi_r0 + r;
+        const int b = win_base(d, row >> k1, row & mask);
+        int j = lo - b;
+        if (j < 0) j += W;
+        if (whole && j >= L && j + kV <= W) continue;   // all 8 outside the window
+        Acc asc[kV];
+#pragma unroll
+        for (int k = 0; k < kV; ++k) asc[k] = SG > 0 ? v[r][k] : v[r][kV - 1 - k];
+        DstE *rp = base + (int64_t)row * d.hi.pitch;
+        if (whole && j + kV <= L) {
+            store8<DstE, Acc>(rp, j, L, asc);
+        } else {
+            Vec8<Acc> e;
+#pragma unroll
+            for (int k = 0; k < kV; ++k) e.x[k] = asc[k];
+            store_win_edge<Acc, DstE>(rp, lo, b, W, L, e);
+        }
+    }
+}
+
+// Does any of the R rows hi_r0.. of a windowed adjoint level take a column
+// of [xa, xa + len)? (warp-uniform: decides whether a block-B item runs)
+template <int R>
+__device__ __forceinline__ bool win_rows_hit(const PassDesc &d, int k1, int hi_r0, int xa,
+                                             int len) {
+    const int W = d.W, L = d.win_len, mask = (1 << k1) - 1;
+    if (xa >= W) return false;
+    if (len > W - xa) len = W - xa;
+    bool hit = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = hi_r0 + r;
+        int j = xa - win_base(d, row >> k1, row & mask);
+        if (j < 0) j += W;
+        hit |= j < L || j + len > W;
+    }
+    return hit;
 }
 
 // Final level of an adjoint: R consecutive output rows y0.. (image rows of the
@@ -853,6 +943,17 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
         // when none is used later
         const int slope0 = (ip.a << M) + a2 * RB;
         if (slope0 > d.need_hi || slope0 + RB - 1 < d.need_lo) continue;
+        if constexpr (ADJ && !FIN) {
+            // windowed level: skip the item when no row's window meets the
+            // warp's columns
+            if (d.hi_win) {
+                const int c0 = jc * kWarpValid;
+                const int cnt = T - c0 < kWarpValid ? T - c0 : kWarpValid;
+                const int xa = SG > 0 ? ip.D + c0 : ip.D - c0 - cnt + 1;
+                if (!win_rows_hit<RB>(d, d.k0 + M, hi_row(d, M, ip.S, ip.a, a2 * RB), xa, cnt))
+                    continue;
+            }
+        }
         const int i0 = jc * kWarpValid + lane * kV;
         Acc v[RB][kV];
         if (!ip.black) {
@@ -880,6 +981,9 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
             if constexpr (ADJ && FIN) {
                 store_image_block<SG, FIN == 2, RB, Acc, DstE>(d, hi_row(d, M, ip.S, ip.a, a2 * RB), dc.lo,
                                                      v);
+            } else if (ADJ && !FIN && d.hi_win) {
+                store_rows_win<SG, RB, Acc, DstE>(d, d.k0 + M, dc.lo,
+                                                  hi_row(d, M, ip.S, ip.a, a2 * RB), v);
             } else {
                 store_rows<SG, FIN, RB, Acc, DstE>(d, dc, hi_row(d, M, ip.S, ip.a, a2 * RB), v);
             }
@@ -924,6 +1028,9 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
                 const DestCols dc = dest_cols<SG, FIN, Acc, DstE>(d, ip.D, i0);
                 if constexpr (ADJ && FIN) {
                     store_image_block<SG, FIN == 2, RA, Acc, DstE>(d, hi_row(d, M, ip.S, ip.a, 0), dc.lo, v);
+                } else if (ADJ && !FIN && d.hi_win) {
+                    store_rows_win<SG, RA, Acc, DstE>(d, d.k0 + M, dc.lo,
+                                                      hi_row(d, M, ip.S, ip.a, 0), v);
                 } else {
                     store_rows<SG, FIN, RA, Acc, DstE>(d, dc, hi_row(d, M, ip.S, ip.a, 0), v);
                 }

@@ -30,10 +30,10 @@ inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t 
         rd = d.cyclic ? (double)(d.src_t_last - d.src_t_first + 1) * d.W * src_bytes
                       : (double)d.lo.rows * d.lo.cols * src_bytes;
     } else {
-        rd = rows * d.lo.cols * src_bytes;
+        rd = rows * (d.lo_win ? d.win_len : d.lo.cols) * src_bytes;
     }
     if (!d.hi_final) {
-        wr = rows * d.hi.cols * dst_bytes;
+        wr = rows * (d.hi_win ? d.win_len : d.hi.cols) * dst_bytes;
     } else if (d.dst_image) {
         wr = (double)d.dst_h * d.dst_w * dst_bytes * (d.accumulate ? 2 : 1);
     } else {

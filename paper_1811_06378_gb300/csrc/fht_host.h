@@ -38,6 +38,23 @@ unsigned int read_device_counters();
 // (FHT_PIPE=1 in the environment turns it on; off by default).
 bool pipe_enabled();
 
+// Window of the level an adjoint's final pass reads (final pass of Mf levels,
+// cropped to the w_c columns p in [p_begin, p_begin + w_c), p_begin = n for
+// sign +1 and 0 for sign -1): row (s, a) is read on the w_c + 2^Mf - 1
+// columns from c + sigma*a*s, c = 2^(K - Mf) for sign +1 (the final level's
+// columns sit 2^K - 2^(K - Mf) past the level's) and -(2^Mf - 1) for sign -1.
+// The stored window starts 8 to 15 columns earlier (win_base), so it is 15
+// columns longer, rounded up to 8. 0 when the window would not save anything
+// (it must stay 16 columns short of W).
+inline void adjoint_window(int w_c, int W, int K, int Mf, int sigma, int *len, int *c) {
+    const int L = (w_c + (1 << Mf) - 1 + 15 + 7) / 8 * 8;
+    *len = 0;
+    *c = 0;
+    if (L + 16 > W) return;
+    *len = L;
+    *c = sigma > 0 ? (1 << (K - Mf)) : W - ((1 << Mf) - 1);
+}
+
 template <typename T> inline const char *acc_name();
 template <> inline const char *acc_name<float>() { return "f32"; }
 template <> inline const char *acc_name<int32_t>() { return "i32"; }

@@ -186,6 +186,29 @@ def test_adjoint_full(fht, h, w):
     assert (got == O.adjoint_full(g, h, w, "f32")).all()
 
 
+@pytest.mark.parametrize("h,w,q", [(1500, 300, 0), (300, 1500, 3), (1000, 77, 1),
+                                   (8192, 200, 1), (200, 8192, 2)])
+def test_adjoint_quadrant_multi_pass_exact(fht, h, w, q):
+    """Two-pass (K = 10, 11) and three-pass (K = 13) quadrant adjoints, whose
+    last intermediate level keeps only the columns its final pass reads,
+    every element bit-exact against the oracle's FP32 recursion."""
+    n, W = O.quadrant_geometry(h, w, q)
+    g = np.random.default_rng(h + 3 * w + q).standard_normal((n, W)).astype(np.float32)
+    got = host(fht.adjoint(dev(g), h, w, fht.LAYOUT_QUADRANT, q))
+    assert (got == O.adjoint_quadrant(g, h, w, q, "f32")).all()
+
+
+def test_adjoint_full_4096_complete(fht):
+    """The benchmark's adjoint: a 16381 x 8192 FP32 gradient back-projected
+    onto the 4096 x 4096 image (four quadrants, two passes each), every
+    element bit-exact against the oracle's FP32 recursion."""
+    R, W = O.full_geometry(4096, 4096)
+    g = np.random.default_rng(4096).standard_normal((R, W), dtype=np.float32)
+    got = host(fht.adjoint(dev(g), 4096, 4096, fht.LAYOUT_FULL))
+    assert (got == O.adjoint_full(g, 4096, 4096, "f32")).all()
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("h,w", [(32, 32), (50, 77)])
 def test_dot_product_on_gpu(fht, h, w):
     """<F x, y> = <x, F^T y>, both sides computed by the CUDA kernels."""
