@@ -38,7 +38,8 @@ with gcc, no fast-math). Readings of points the paper leaves open:
 7. Angle ranges map to slopes by t = (n-1)*tan(theta); see ``angle_to_slopes``.
 8. The shear of Section 4 (``sheared_quadrant``): row y of the (transposed)
    image is shifted cyclically right by s(y) = floor(y*spl + 1/2) columns
-   (spl = "shift per line"; the paper gives no rounding), then the plain
+   (spl = "shift per line"; the paper gives no rounding), evaluated exactly
+   with spl in fixed point (32 fractional bits, rounded half up), then the plain
    quadrant transform runs on the cyclic width W = w + n, which the paper
    keeps ("the black zone will simply move").
 """
@@ -336,14 +337,18 @@ def angle_to_slopes(phi_lo: float, phi_hi: float, h: int, w: int
 
 # ---------------------------------------------------------------- shear (Section 4)
 
+def shear_fixed(spl: float) -> int:
+    """spl in fixed point with 32 fractional bits, rounded half up:
+    P = floor(spl * 2^32 + 1/2) (exact in float64 for |spl| <= 1)."""
+    return int(math.floor(float(spl) * 2.0**32 + 0.5))
+
+
 def shear_shifts(rows: int, spl: float) -> np.ndarray:
-    """s(y) = floor(y*spl + 1/2) for y < rows: the shift per line of Section 4
-    rounded half up, the product and the sum each rounded to float64 (no fused
-    multiply-add), so that an integer decision taken from the same double
-    arithmetic elsewhere agrees."""
-    y = np.arange(rows, dtype=np.float64)
-    prod = y * np.float64(spl)
-    return np.floor(prod + np.float64(0.5)).astype(np.int64)
+    """s(y) = floor(y*spl + 1/2) for y < rows, the shift per line of Section 4
+    rounded half up, evaluated exactly on the 32-bit fixed-point spl:
+    s(y) = floor((y*P + 2^31) / 2^32), P = shear_fixed(spl)."""
+    P = shear_fixed(spl)
+    return np.array([(y * P + 2**31) >> 32 for y in range(rows)], dtype=np.int64)
 
 
 def sheared_quadrant(img: np.ndarray, q: int, spl: float, kind: str = "i64",

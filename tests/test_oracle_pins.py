@@ -422,7 +422,14 @@ def test_sampled_points_match_full_transform():
 
 def test_shear_shifts_round_half_up():
     """s(y) = floor(y*spl + 1/2): exact halves round up, negative shifts round
-    towards +infinity at halves, spl = 0 gives no shift."""
+    towards +infinity at halves, spl = 0 gives no shift; with spl in 32-bit
+    fixed point the result equals the real-number formula away from halves."""
+    rng = np.random.default_rng(0)
+    for spl in rng.uniform(-1, 1, 20):
+        ys = np.arange(4096)
+        exact = np.floor(ys * spl + 0.5)
+        near_half = np.abs((ys * spl + 0.5) - np.round(ys * spl + 0.5)) < 1e-6
+        assert (O.shear_shifts(4096, spl)[~near_half] == exact[~near_half]).all()
     assert list(O.shear_shifts(5, 0.5)) == [0, 1, 1, 2, 2]
     assert list(O.shear_shifts(5, -0.5)) == [0, 0, -1, -1, -2]
     assert list(O.shear_shifts(4, 0.0)) == [0, 0, 0, 0]
