@@ -194,6 +194,46 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
                        void *grad_img, int64_t out_pitch, void *workspace,
                        size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------ sheared (Section 4)
+ * The paper's way to a chosen range of line angles: shear the image
+ * horizontally by spl ("shift per line") inside the first butterfly
+ * iteration, then run one quadrant. Row y of the image (of the transposed
+ * image for Q2/Q3) is taken as rotated right by s(y) = floor(y*spl + 1/2)
+ * columns modulo W (the paper fixes no rounding; it is evaluated exactly with
+ * spl in fixed point, P = floor(spl * 2^32 + 1/2), s(y) = (y*P + 2^31) >> 32),
+ * zero outside the image, so that
+ *   Hs[t][x] = sum_{y<n} P[y][(x + sigma*off_n(t,y) - s(y)) mod W].
+ * A line with dx/dy = k then lies on slope k + spl: the quadrant's slopes
+ * t/(n-1) in [0, 1] cover k in [-spl, 1 - spl] (Q0; columns per row of the
+ * transposed image for Q2/Q3). The shear moves the black zone, so every
+ * intermediate level is all W columns wide (cyclic); no fhtshift. */
+
+/* Workspace bytes of fht_forward_sheared for this size, quadrant and types. */
+fht_status fht_workspace_size_sheared(int h, int w, fht_quadrant q, fht_dtype in_t,
+                                      fht_dtype acc_t, size_t *bytes);
+
+/* Slope rows t_lo..t_hi of the sheared quadrant q into out ((t_hi - t_lo + 1)
+ * x W, pitch out_pitch >= W; row t at out row t - t_lo); -1 <= spl <= 1
+ * (FHT_EINVAL otherwise, NaN included); types as fht_forward. Only the slopes
+ * those rows depend on are computed (the range pruning of fht_forward_range).
+ * spl = 0 gives exactly fht_forward_range. */
+fht_status fht_forward_sheared(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                               fht_quadrant q, double spl, int t_lo, int t_hi, void *out,
+                               fht_dtype acc_t, int64_t out_pitch, void *workspace,
+                               size_t workspace_bytes, void *stream);
+
+/* One sheared quadrant for the line angles [phi_lo, phi_hi] (degrees, the
+ * quadrant spans of fht_angle_to_slopes), host only. A mostly vertical range
+ * (inside [-45, 45]) gives Q0 and spl = tan(phi_hi): row t holds the angle
+ * atan(spl - t/(n-1)), phi_hi at t = 0. A mostly horizontal range (inside
+ * [45, 135]) gives Q3 and spl = -tan(phi_lo - 90): row t holds
+ * 90 + atan(t/(n-1) - spl), phi_lo at t = 0. t_lo = 0 and t_hi =
+ * floor((n-1)*(tan(b) - tan(a))), a, b the range's ends measured from the
+ * axis. FHT_EINVAL if the range crosses 45 or 135 degrees or its ends differ
+ * by more than 1 in tangent. */
+fht_status fht_shear_range(double phi_lo, double phi_hi, int h, int w, fht_quadrant *q,
+                           double *spl, int *t_lo, int *t_hi);
+
 /* ------------------------------------------------------------ uniform batches
  * `batch` transforms of the same size and layout in one launch per pass (the
  * launch's third grid dimension is the image), so that many small images fill

@@ -65,6 +65,9 @@ def _load() -> ctypes.CDLL:
         "fht_full_quadrants": (i, [vp, i, i, i, i64, vp, i, i64, i, vp, sz, vp]),
         "fhtshift": (i, [vp, vp, i, i, i, i, i, i, i64, i64, vp]),
         "fht_adjoint": (i, [vp, i, i, i, i, i, i64, vp, i64, vp, sz, vp]),
+        "fht_workspace_size_sheared": (i, [i, i, i, i, i, ctypes.POINTER(sz)]),
+        "fht_forward_sheared": (i, [vp, i, i, i, i64, i, d, i, i, vp, i, i64, vp, sz, vp]),
+        "fht_shear_range": (i, [d, d, i, i, ip, ctypes.POINTER(d), ip, ip]),
         "fht_plan_create_batched": (i, [ctypes.POINTER(i), ctypes.POINTER(i), i, i, i, i,
                                         ctypes.POINTER(vp), ctypes.POINTER(sz)]),
         "fht_forward_batched": (i, [vp, vp, vp, sz, vp]),
@@ -270,6 +273,48 @@ def adjoint(grad: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: in
 
 
 # ------------------------------------------------------------------ batched
+
+# ------------------------------------------------------------------ sheared (Section 4)
+
+def workspace_size_sheared(h: int, w: int, q: int, in_dtype: torch.dtype,
+                           acc: torch.dtype) -> int:
+    n = ctypes.c_size_t()
+    _check(lib.fht_workspace_size_sheared(h, w, q, _DTYPE[in_dtype], _DTYPE[acc],
+                                          ctypes.byref(n)), "fht_workspace_size_sheared")
+    return n.value
+
+
+def shear_range(phi_lo: float, phi_hi: float, h: int, w: int) -> tuple[int, float, int, int]:
+    """(q, spl, t_lo, t_hi): the one sheared quadrant and its slope rows for
+    the line angles [phi_lo, phi_hi] degrees (fht_shear_range)."""
+    q, t_lo, t_hi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    spl = ctypes.c_double()
+    _check(lib.fht_shear_range(phi_lo, phi_hi, h, w, ctypes.byref(q), ctypes.byref(spl),
+                               ctypes.byref(t_lo), ctypes.byref(t_hi)), "fht_shear_range")
+    return q.value, spl.value, t_lo.value, t_hi.value
+
+
+def forward_sheared(img: torch.Tensor, q: int, spl: float, t_lo: int = 0,
+                    t_hi: int | None = None, acc: torch.dtype = torch.int32,
+                    out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """Rows t_lo..t_hi of quadrant q of the image sheared by spl per row
+    (Section 4; fht_forward_sheared)."""
+    in_code, in_pitch = _dev2d(img, "img")
+    h, w = img.shape
+    n, W = query_shape(h, w, q)
+    t_hi = n - 1 if t_hi is None else t_hi
+    if out is None:
+        out = torch.empty((t_hi - t_lo + 1, W), dtype=acc, device=img.device)
+    out_code, out_pitch = _dev2d(out, "out")
+    _shape(out, (t_hi - t_lo + 1, W), "out")
+    ws = _workspace(workspace, workspace_size_sheared(h, w, q, img.dtype, out.dtype),
+                    img.device)
+    _check(lib.fht_forward_sheared(_ptr(img), in_code, h, w, in_pitch, q, float(spl), t_lo,
+                                   t_hi, _ptr(out), out_code, out_pitch, _ptr(ws), _nbytes(ws),
+                                   _stream(stream)), "fht_forward_sheared")
+    return out
+
 
 class BatchPlan:
     """Many images of different sizes, each transformed as `forward` would

@@ -112,6 +112,7 @@ int split_levels(int K, int *m) {
 struct QuadPlan {
     int q, sigma, transpose;
     bool adjoint;
+    bool cyclic;        // every level all W columns wide, read cyclically
     int in_elem, acc_elem;
     int h_c, w_c;       // content size of the (transposed) image
     int n, K, W;
@@ -130,11 +131,15 @@ struct QuadPlan {
 // Plan of quadrant q. With `adjoint`, the plan is the transform's transpose:
 // the opposite-sign transform of the gradient (the dyadic offsets are
 // symmetric in slope and row), every level all W columns wide and cyclic.
+// With `sheared`, the quadrant's own transform of the sheared image (Section
+// 4), also on cyclic full-width levels: the shear moves the black zone, so
+// the compact columns do not hold.
 QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
-                   bool adjoint = false) {
+                   bool adjoint = false, bool sheared = false) {
     QuadPlan P{};
     P.q = q;
     P.adjoint = adjoint;
+    P.cyclic = adjoint || sheared;
     P.in_elem = in_elem;
     P.acc_elem = acc_elem;
     P.transpose = q >= 2;
@@ -164,7 +169,7 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
         // u8 images summed over 2^k rows stay below 2^16 while k <= 8
         if (acc_elem == kI32 && in_elem == kU8 && k <= 8 && !adjoint) type = kU16;
         P.lvl_type[p] = type;
-        P.lvl_cols[p] = adjoint ? P.W : std::min(P.W, P.w_c + (1 << k));
+        P.lvl_cols[p] = P.cyclic ? P.W : std::min(P.W, P.w_c + (1 << k));
         P.lvl_pitch[p] = (int64_t)align_up(P.lvl_cols[p], 64);
         if (P.win_len > 0 && p == P.npass - 1) {
             // windowed: loads of 8 from any index below win_len stay in the row
@@ -322,7 +327,7 @@ PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &fina
     d.s_count = P.n >> P.k[p + 1];
     d.p_begin = 0;
     d.p_count = d.hi.cols;
-    d.cyclic = P.adjoint ? 1 : 0;
+    d.cyclic = P.cyclic ? 1 : 0;
     d.t_first = fm.t_first;
     d.t_last = fm.t_last;
     d.row_base = fm.row_base;
@@ -740,6 +745,108 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
                                    workspace, st);
         if (s != FHT_OK) return s;
     }
+    return FHT_OK;
+}
+
+// ------------------------------------------------------------ sheared (Section 4)
+
+static bool spl_ok(double spl) { return spl >= -1.0 && spl <= 1.0; }   // false for NaN
+
+fht_status fht_workspace_size_sheared(int h, int w, fht_quadrant q, fht_dtype in_t,
+                                      fht_dtype acc_t, size_t *bytes) {
+    if (!sizes_ok(h, w) || !quadrant_ok(q) || !bytes) return FHT_EINVAL;
+    const int acc = acc_kind(in_t, acc_t);
+    if (acc < 0) return FHT_EINVAL;
+    *bytes = plan_workspace(make_plan(h, w, q, false, elem_of(in_t), acc, false, true));
+    return FHT_OK;
+}
+
+fht_status fht_forward_sheared(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                               fht_quadrant q, double spl, int t_lo, int t_hi, void *out,
+                               fht_dtype acc_t, int64_t out_pitch, void *workspace,
+                               size_t workspace_bytes, void *stream) {
+    if (!img || !out || !sizes_ok(h, w) || !quadrant_ok(q) || in_pitch < w || !spl_ok(spl))
+        return FHT_EINVAL;
+    const int acc = acc_kind(in_t, acc_t);
+    if (acc < 0) return FHT_EINVAL;
+    const int in_elem = elem_of(in_t);
+    QuadPlan P = make_plan(h, w, q, false, in_elem, acc, false, true);
+    if (P.K > kMaxK) return FHT_EINVAL;
+    if (t_lo < 0 || t_hi < t_lo || t_hi >= P.n || out_pitch < P.W) return FHT_EINVAL;
+    const size_t need = plan_workspace(P);
+    if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
+    Side image{const_cast<void *>(img), in_pitch, in_elem, P.h_c, P.w_c};
+    Side o{out, out_pitch, elem_of(acc_t), 0, P.W};
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int p = 0; p < P.npass; ++p) {
+        PassDesc d = pass_desc(P, p, image, o, workspace, quadrant_map(t_lo, t_hi), t_lo, t_hi);
+        d.shear_on = 1;
+        // spl in fixed point, 32 fractional bits, rounded half up (exact in
+        // double for |spl| <= 1)
+        d.shear_p = (long long)std::floor(spl * 4294967296.0 + 0.5);
+        if (d.hi_final) {
+            // every column X of the slope rows [t_lo, t_hi]: p = X + sigma_plus * n
+            d.dst_image = 1;
+            d.dst_row_lo = t_lo;
+            d.dst_h = t_hi + 1;
+            d.dst_w = P.W;
+            d.dst_transpose = 0;
+            d.accumulate = 0;
+            d.hi.cols = P.W;
+            d.p_begin = P.sigma > 0 ? P.n : 0;
+            d.p_count = P.W;
+        }
+        // cyclic pass code for the pass's element types (a uint8 image's
+        // first level is uint16, as in the compact forward)
+        cudaError_t e;
+        if (acc == kF32)
+            e = d.lo.type == kU8 ? launch_adjoint_f32_u8(P.m[p], d, st)
+                                 : launch_adjoint_f32(P.m[p], d, st);
+        else if (d.lo.type == kU8)
+            e = d.hi.type == kU16 ? launch_adjoint_i32_u8_u16(P.m[p], d, st)
+                                  : launch_adjoint_i32_u8(P.m[p], d, st);
+        else if (d.lo.type == kU16)
+            e = launch_adjoint_i32_u16(P.m[p], d, st);
+        else
+            e = launch_adjoint_i32(P.m[p], d, st);
+        if (e != cudaSuccess) {
+            g_last_cuda_error = (int)e;
+            return FHT_ECUDA;
+        }
+    }
+    return FHT_OK;
+}
+
+fht_status fht_shear_range(double phi_lo, double phi_hi, int h, int w, fht_quadrant *q,
+                           double *spl, int *t_lo, int *t_hi) {
+    if (!q || !spl || !t_lo || !t_hi || !sizes_ok(h, w) || !(phi_lo <= phi_hi))
+        return FHT_EINVAL;
+    const double rad = M_PI / 180.0;
+    int qq;
+    double a, b, s;
+    if (phi_lo >= -45.0 && phi_hi <= 45.0) {
+        qq = FHT_Q0;
+        a = phi_lo;
+        b = phi_hi;
+        s = std::tan(b * rad);
+    } else if (phi_lo >= 45.0 && phi_hi <= 135.0) {
+        qq = FHT_Q3;
+        a = phi_lo - 90.0;
+        b = phi_hi - 90.0;
+        s = -std::tan(a * rad);
+    } else {
+        return FHT_EINVAL;
+    }
+    const double span = std::tan(b * rad) - std::tan(a * rad);
+    if (span > 1.0 + 1e-12) return FHT_EINVAL;
+    int rows = 0, cols = 0;
+    fht_query_shape(h, w, (fht_quadrant)qq, &rows, &cols);
+    int hi = 0;
+    if (rows > 1) hi = std::min(rows - 1, (int)std::floor((rows - 1) * span + 1e-9));
+    *q = (fht_quadrant)qq;
+    *spl = s;
+    *t_lo = 0;
+    *t_hi = hi;
     return FHT_OK;
 }
 

@@ -83,6 +83,15 @@ struct PassDesc {
     // j = (x - base) mod W < win_len; its pitch is >= win_len + 8. hi_win:
     // this pass writes such a level; lo_win: it reads one.
     int lo_win, hi_win, win_len, win_c;
+    // Sheared forward (Section 4), set on every pass of it; it runs on the
+    // cyclic (adjoint) pass code with the quadrant's own sign: the level-0
+    // source is the (transposed) image whose row y is rotated right by
+    // s(y) = (y*shear_p + 2^31) >> 32 columns modulo W (floor(y*spl + 1/2)
+    // with spl in 32-bit fixed point, shear_p = floor(spl*2^32 + 1/2)), zero
+    // outside its lo.rows x lo.cols content; the final level goes to the
+    // quadrant's rows t in [dst_row_lo, dst_h), stored at row t - dst_row_lo.
+    int shear_on, dst_row_lo;
+    long long shear_p;
 };
 
 __host__ __device__ inline int64_t floor_mod(int64_t v, int64_t m) {

@@ -390,6 +390,76 @@ __device__ __noinline__ Block<Acc, RA> load_block_a_edge(const PassDesc &d, int 
     return b;
 }
 
+// Shift of sheared image row y: floor(y*spl + 1/2) on the 32-bit fixed-point
+// spl, exact in 64-bit integers (|y * shear_p| < 2^47).
+__device__ __forceinline__ int shear_shift(const PassDesc &d, int y) {
+    return (int)(((long long)y * d.shear_p + (1LL << 31)) >> 32);
+}
+
+// Rare sheared loads: the 8 columns wrap past W, or the image is read
+// transposed (8 image rows of one column).
+template <typename Acc, typename SrcE>
+__device__ __noinline__ Vec8<Acc> load8_sheared_edge(const PassDesc &d, const SrcE *img, int y,
+                                                     int c0) {
+    Vec8<Acc> r;
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        int c = c0 + k;
+        if (c >= d.W) c -= d.W;
+        Acc v = Acc(0);
+        if (c < d.lo.cols)
+            v = d.transpose ? (Acc)img[(int64_t)c * d.lo.pitch + y]
+                            : (Acc)img[(int64_t)y * d.lo.pitch + c];
+        r.x[k] = v;
+    }
+    return r;
+}
+
+// Block A's source rows of a sheared forward's first pass: image row
+// row0 + r (an image column for the transposed quadrants) rotated right by
+// its shear shift, cyclically on W, zero outside the image; this lane's 8
+// ascending columns start at X (buffer order after the reverse for sign -1).
+template <int SG, int RA, typename Acc, typename SrcE>
+__device__ __forceinline__ void load_block_a_sheared(const PassDesc &d, int row0, int X,
+                                                     int Xw0, int Xw1, Acc (&v)[RA][kV]) {
+    const SrcE *img = reinterpret_cast<const SrcE *>(d.lo.ptr);
+    if (!d.transpose && row0 + RA <= d.lo.rows) {
+        // Whether every row's columns for the whole warp ([Xw0, Xw1) less the
+        // row's shift) lie inside the image is decided once, warp-uniformly,
+        // from the first and last row (the shifts are monotone in y); then all
+        // rows' loads are issued without branches.
+        const int sa = shear_shift(d, row0), sb = shear_shift(d, row0 + RA - 1);
+        const int s_lo = sa < sb ? sa : sb, s_hi = sa < sb ? sb : sa;
+        if (Xw0 - s_hi >= 0 && Xw1 - s_lo <= d.lo.cols) {
+            const SrcE *p0 = img + (int64_t)row0 * d.lo.pitch;
+#pragma unroll
+            for (int r = 0; r < RA; ++r) {
+                load8_fast<SrcE, Acc>(p0 + r * d.lo.pitch, X - shear_shift(d, row0 + r), v[r]);
+                if constexpr (SG < 0) reverse8(v[r]);
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RA; ++r) {
+        const int y = row0 + r;
+        if (y >= d.lo.rows) {
+#pragma unroll
+            for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
+            continue;
+        }
+        const int c0 = wrap_w(X - shear_shift(d, y), d.W);
+        if (!d.transpose && c0 + kV <= d.W) {
+            load8<SrcE, Acc>(img + (int64_t)y * d.lo.pitch, c0, d.lo.cols, v[r]);
+        } else {
+            const Vec8<Acc> e = load8_sheared_edge<Acc, SrcE>(d, img, y, c0);
+#pragma unroll
+            for (int k = 0; k < kV; ++k) v[r][k] = e.x[k];
+        }
+        if constexpr (SG < 0) reverse8(v[r]);
+    }
+}
+
 // Block A's RA source rows s0.. for this lane's 8 buffer columns i0..i0+7.
 // Whether every row and every lane of the warp item (columns wbase ..
 // wbase + 255) lies inside the source is decided once, warp-uniformly; the
@@ -400,6 +470,16 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
     constexpr int sg = SG;
     const int splus = sg > 0 ? 1 : 0;
     if constexpr (ADJ) {
+        if (d.lo_image && d.shear_on) {
+            // sheared forward, first pass: a = 0 (level 0 has one slope)
+            const int p_first = A_off + sg * i0;
+            const int X = (sg > 0 ? p_first : p_first - (kV - 1)) - splus;
+            // ascending columns of the whole warp item: [Xw0, Xw1)
+            const int Xw0 = sg > 0 ? A_off + wbase - splus : A_off - wbase - (32 * kV - 1);
+            load_block_a_sheared<SG, RA, Acc, SrcE>(d, S * (1 << M) + s0, X, Xw0, Xw0 + 32 * kV,
+                                                    v);
+            return;
+        }
         if (!d.lo_image && d.lo_win) {
             // windowed level: row s0 + r of group a at its stored index; the
             // 8 columns never wrap inside a window (win_len <= W - 16), and
@@ -720,12 +800,13 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
         const bool vec = inside && (X0 & 3) == 0 && (pitch & 3) == 0 &&
                          ((reinterpret_cast<uintptr_t>(img) & 15) == 0);
         const int rows = d.dst_h - y0;   // rows r < rows exist
+        const int r_lo = d.dst_row_lo - y0;   // ... and rows r >= r_lo
         if (vec) {
-            DstE *base = img + (int64_t)y0 * pitch + X0;
+            DstE *base = img + (int64_t)(y0 - d.dst_row_lo) * pitch + X0;
             if (!acc) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    if (r >= rows) continue;
+                    if (r >= rows || r < r_lo) continue;
                     V4 a, b;
                     a.x = (DstE)v[r][sg > 0 ? 0 : 7];
                     a.y = (DstE)v[r][sg > 0 ? 1 : 6];
@@ -747,7 +828,7 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
                 V4 old[B][2];
 #pragma unroll
                 for (int j = 0; j < B; ++j) {
-                    if (r0 + j < rows) {
+                    if (r0 + j < rows && r0 + j >= r_lo) {
                         const V4 *q = reinterpret_cast<const V4 *>(base + (r0 + j) * pitch);
                         old[j][0] = q[0];
                         old[j][1] = q[1];
@@ -756,7 +837,7 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
 #pragma unroll
                 for (int j = 0; j < B; ++j) {
                     const int r = r0 + j;
-                    if (r >= rows) continue;
+                    if (r >= rows || r < r_lo) continue;
                     Acc asc[kV];
 #pragma unroll
                     for (int k = 0; k < kV; ++k) asc[k] = sg > 0 ? v[r][k] : v[r][kV - 1 - k];
@@ -777,12 +858,12 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                if (r >= rows) continue;
+                if (r >= rows || r < r_lo) continue;
                 Vec8<Acc> a;
 #pragma unroll
                 for (int k = 0; k < kV; ++k) a.x[k] = sg > 0 ? v[r][k] : v[r][kV - 1 - k];
-                store_image_row_edge<Acc, DstE>(img + (int64_t)(y0 + r) * pitch, X0, lo, p_lo,
-                                                p_hi, acc, a);
+                store_image_row_edge<Acc, DstE>(img + (int64_t)(y0 + r - d.dst_row_lo) * pitch,
+                                                X0, lo, p_lo, p_hi, acc, a);
             }
         }
     } else {

@@ -27,15 +27,16 @@ inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t 
     const double rows = (double)d.s_count * d.a_count * (1 << M);
     double rd, wr;
     if (d.lo_image) {
-        rd = d.cyclic ? (double)(d.src_t_last - d.src_t_first + 1) * d.W * src_bytes
-                      : (double)d.lo.rows * d.lo.cols * src_bytes;
+        rd = d.cyclic && !d.shear_on
+                 ? (double)(d.src_t_last - d.src_t_first + 1) * d.W * src_bytes
+                 : (double)d.lo.rows * d.lo.cols * src_bytes;
     } else {
         rd = rows * (d.lo_win ? d.win_len : d.lo.cols) * src_bytes;
     }
     if (!d.hi_final) {
         wr = rows * (d.hi_win ? d.win_len : d.hi.cols) * dst_bytes;
     } else if (d.dst_image) {
-        wr = (double)d.dst_h * d.dst_w * dst_bytes * (d.accumulate ? 2 : 1);
+        wr = (double)(d.dst_h - d.dst_row_lo) * d.dst_w * dst_bytes * (d.accumulate ? 2 : 1);
     } else {
         const int t0 = d.a_lo << M, t1 = ((d.a_lo + d.a_count) << M) - 1;
         const int lo = t0 > d.t_first ? t0 : d.t_first, hi = t1 < d.t_last ? t1 : d.t_last;
@@ -281,7 +282,10 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     char name[64];
-    snprintf(name, sizeof name, "%s_m%d_%s%s%s", ADJ ? "adjoint_fused" : "forward_fused",
+    snprintf(name, sizeof name, "%s_m%d_%s%s%s",
+             d.shear_on ? "sheared_fused"
+             : ADJ                                   ? "adjoint_fused"
+                                                     : "forward_fused",
              MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "", d.batch > 1 ? "_batch" : "");
     LaunchScope scope(name, st,
                       d.batch * pass_alg_bytes(d, MA + MB, sizeof(SrcE), sizeof(DstE)));

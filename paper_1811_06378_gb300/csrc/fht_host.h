@@ -71,5 +71,11 @@ cudaError_t launch_fused_f32_f32(int M, const PassDesc &d, cudaStream_t st);
 // Adjoint passes: the opposite-sign cyclic transform of a gradient.
 cudaError_t launch_adjoint_f32(int M, const PassDesc &d, cudaStream_t st);
 cudaError_t launch_adjoint_i32(int M, const PassDesc &d, cudaStream_t st);
+// The same cyclic pass code over a uint8 image: first passes of the sheared
+// forward transform.
+cudaError_t launch_adjoint_f32_u8(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_adjoint_i32_u8(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_adjoint_i32_u8_u16(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_adjoint_i32_u16(int M, const PassDesc &d, cudaStream_t st);
 
 }  // namespace fht

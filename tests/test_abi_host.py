@@ -140,3 +140,41 @@ def test_bad_arguments_rejected_on_host(fht):
     lo = (ctypes.c_int * 4)()
     assert L.fht_angle_to_slopes(10.0, 5.0, 8, 8, lo, lo) == EINVAL
     assert fht.lib.fht_status_string(EINVAL) == b"invalid argument"
+
+
+@pytest.mark.parametrize("rng_", [(-15, 15), (75, 105), (-45, 0), (0, 45), (-45, 45),
+                                  (-20, -5), (60, 100), (45, 90), (90, 135), (30, 60),
+                                  (-30, 30), (10, 10), (-50, 0)])
+@pytest.mark.parametrize("hw", [(2048, 2048), (256, 100), (1, 1), (7, 300)])
+def test_shear_range_matches_oracle(fht, rng_, hw):
+    want = O.shear_range(float(rng_[0]), float(rng_[1]), *hw)
+    if want is None:
+        with pytest.raises(fht.FHTError):
+            fht.shear_range(float(rng_[0]), float(rng_[1]), *hw)
+        return
+    got = fht.shear_range(float(rng_[0]), float(rng_[1]), *hw)
+    assert got[0] == want[0] and got[2:] == want[2:]
+    assert got[1] == want[1]   # the same double arithmetic on both sides
+
+
+def test_sheared_bad_arguments_rejected_on_host(fht):
+    L = fht.lib
+    fake, null, st = ctypes.c_void_p(0x10000), ctypes.c_void_p(0), ctypes.c_void_p(0)
+    U8, I32 = 0, 1
+    ok = dict(spl=0.5, lo=0, hi=7)
+    args = lambda spl, lo, hi, pitch=16: (fake, U8, 8, 8, 8, 0, spl, lo, hi, fake, I32,  # noqa
+                                          pitch, null, 0, st)
+    assert L.fht_forward_sheared(*args(1.5, 0, 7)) == EINVAL
+    assert L.fht_forward_sheared(*args(-1.0001, 0, 7)) == EINVAL
+    assert L.fht_forward_sheared(*args(float("nan"), 0, 7)) == EINVAL
+    assert L.fht_forward_sheared(*args(ok["spl"], 3, 2)) == EINVAL
+    assert L.fht_forward_sheared(*args(ok["spl"], 0, 8)) == EINVAL
+    assert L.fht_forward_sheared(*args(ok["spl"], 0, 7, 15)) == EINVAL
+    n = ctypes.c_size_t()
+    assert L.fht_workspace_size_sheared(4096, 4096, 0, U8, I32, ctypes.byref(n)) == 0
+    # two passes: one full-width level of n x W (pitch rounded to 64), uint16
+    # for a uint8 image (sums of 2^6 bytes), int32 otherwise
+    assert n.value == 4096 * 8192 * 2
+    assert L.fht_workspace_size_sheared(4096, 4096, 0, I32, I32, ctypes.byref(n)) == 0
+    assert n.value == 4096 * 8192 * 4
+    assert L.fht_workspace_size_sheared(4096, 4096, 4, U8, I32, ctypes.byref(n)) == EINVAL
