@@ -18,6 +18,8 @@ What is computed (Aliev, Ershov, Nikolaev, arXiv:1811.06378):
                    slope-pruning reading returns exactly that slice).
 * ``fhtshift``     per-row cyclic regrouping around the accumulator centre
                    (Section 5).
+* ``point_segment`` the image pixels one Hough point sums (Section 3.2).
+* ``sheared_quadrant`` the quadrant of the sheared image (Section 4).
 * ``adjoint_*``    the transpose of each map (not in the paper; defined by the
                    transform being linear), computed as the opposite-sign
                    transform of the gradient because the dyadic offsets are
@@ -333,6 +335,33 @@ def angle_to_slopes(phi_lo: float, phi_hi: float, h: int, w: int
         if lo[q] > hi[q]:
             lo[q] = hi[q] = -1
     return lo, hi
+
+
+# ---------------------------------------------------------------- Hough point -> segment (Section 3.2)
+
+def point_segment(h: int, w: int, q: int, t: int, x: int):
+    """The part of the image that Hough point (t, x) of quadrant q sums
+    (Section 3.2): the slope-t pattern from column x, taken modulo the
+    extended width W = w + n (case b: a pattern leaving the extended image on
+    the right re-enters the original image on the left), cut to the image
+    (case a); None when no pixel of it lies in the image (case c).
+
+    Returns (count, (r0, c0), (r1, c1)): the number of its pixels inside the
+    image and its first and last one as image (row, column), ordered by the
+    pattern's row y (an image column for Q2/Q3)."""
+    n, W = quadrant_geometry(h, w, q)
+    hc, wc = (w, h) if TRANSPOSED[q] else (h, w)
+    inside = []
+    for y in range(min(n, hc)):
+        c = (x + SIGMA[q] * offset(n, t, y)) % W
+        if c < wc:
+            inside.append((y, c))
+    if not inside:
+        return None
+    (ya, ca), (yb, cb) = inside[0], inside[-1]
+    if TRANSPOSED[q]:
+        return len(inside), (ca, ya), (cb, yb)
+    return len(inside), (ya, ca), (yb, cb)
 
 
 # ---------------------------------------------------------------- shear (Section 4)

@@ -527,3 +527,54 @@ def test_shear_range_horizontal_and_rejections():
     assert O.shear_range(30.0, 60.0, 64, 64) is None
     assert O.shear_range(-30.0, 30.0, 64, 64) is None
     assert O.shear_range(-45.0, 0.0, 64, 64)[3] == 63
+
+
+# --------------------------------------------------------------- point -> segment (Section 3.2)
+
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
+def test_point_segment_is_what_the_point_sums(q):
+    """An image that is 1 exactly on the returned pixels' run (the pattern
+    between the two ends, rows in between included) and 0 elsewhere makes
+    the Hough point's value the returned count; a random image's value at
+    the point is the sum over those pixels. Covers every point of a small
+    quadrant, cases a, b and c included."""
+    h, w = 9, 14
+    img = random_image(h, w, "u8", seed=q)
+    H = O.quadrant(img, q)
+    n, W = O.quadrant_geometry(h, w, q)
+    ones = O.quadrant(np.ones((h, w), np.uint8), q)
+    for t in range(n):
+        for x in range(W):
+            seg = O.point_segment(h, w, q, t, x)
+            if seg is None:
+                assert H[t, x] == 0 and ones[t, x] == 0
+                continue
+            count, a, b = seg
+            assert ones[t, x] == count
+            # the pixels: the pattern's rows between the two ends
+            tot = 0
+            ya, yb = (a[1], b[1]) if O.TRANSPOSED[q] else (a[0], b[0])
+            for y in range(ya, yb + 1):
+                c = (x + O.SIGMA[q] * O.offset(n, t, y)) % W
+                r, cc = (c, y) if O.TRANSPOSED[q] else (y, c)
+                assert 0 <= r < h and 0 <= cc < w
+                tot += int(img[r, cc])
+            assert tot == H[t, x]
+
+
+def test_point_segment_paper_cases():
+    """Section 3.2 for Q0 of a 6 x 10 image (n = 8, W = 18): (case a) a
+    pattern that leaves the image through its right side keeps the part
+    inside; (case b) one that leaves the extended image re-enters on the left
+    (columns modulo w + n); (case c) one wholly in the extension sums
+    nothing."""
+    h, w = 6, 10
+    # vertical pattern from column 3: all six image rows
+    assert O.point_segment(h, w, 0, 0, 3) == (6, (0, 3), (5, 3))
+    # 45-degree pattern from column 7: rows 0..2 at columns 7..9, then leaves (a)
+    assert O.point_segment(h, w, 0, 7, 7) == (3, (0, 7), (2, 9))
+    # 45-degree pattern from column 15: columns 15, 16, 17 in the extension,
+    # then 18 = 0 (mod 18): rows 3..5 at columns 0..2 (b)
+    assert O.point_segment(h, w, 0, 7, 15) == (3, (3, 0), (5, 2))
+    # vertical pattern in the extension (c)
+    assert O.point_segment(h, w, 0, 0, 12) is None
