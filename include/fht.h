@@ -194,6 +194,32 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
                        void *grad_img, int64_t out_pitch, void *workspace,
                        size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------ back to lines
+ * Host only: the image segment that Hough point (row, col) sums (Section 3.2).
+ * The point's pattern (the dyadic digital line of its slope, from its column)
+ * is taken with columns modulo the extended width W (a pattern that leaves
+ * the extended image on the right re-enters the image on the left: the
+ * paper's case b) and cut to the h x w image (case a). Its in-image pixels are
+ * one run along the pattern: *count receives their number (0 when the
+ * pattern lies wholly in the padding: case c, and the ends are -1), (r0, c0)
+ * and (r1, c1) the image row and column of its first and last pixel in the
+ * pattern's order (down the rows for Q0/Q1, along the columns for Q2/Q3).
+ * layout FHT_LAYOUT_QUADRANT: row = slope t of quadrant q, col in [0, W).
+ * layout FHT_LAYOUT_FULL: row = a row of the full image (q ignored; the
+ * quadrants of the power-of-two-padded image, Section 3.3), col in
+ * [0, h_p + w_p). shifted != 0: the Hough image had fhtshift applied
+ * (Section 5); its rotation is undone first. */
+fht_status fht_segment(int h, int w, fht_layout layout, fht_quadrant q, int row, int col,
+                       int shifted, int *count, int *r0, int *c0, int *r1, int *c1);
+
+/* Per-row maxima of a Hough image (rows x cols, int32 or float32, pitch in
+ * elements): max_out[r] (rows values of dtype) and arg_out[r] (int32) the
+ * largest value of row r and the first column holding it; the strongest line
+ * of each slope. One read of the image; NaN entries give unspecified results.
+ * Not in the paper. */
+fht_status fht_row_argmax(const void *hough, fht_dtype dtype, int rows, int cols, int64_t pitch,
+                          void *max_out, int *arg_out, void *stream);
+
 /* ------------------------------------------------------------ sheared (Section 4)
  * The paper's way to a chosen range of line angles: shear the image
  * horizontally by spl ("shift per line") inside the first butterfly

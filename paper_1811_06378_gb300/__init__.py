@@ -66,6 +66,8 @@ def _load() -> ctypes.CDLL:
         "fhtshift": (i, [vp, vp, i, i, i, i, i, i, i64, i64, vp]),
         "fht_adjoint": (i, [vp, i, i, i, i, i, i64, vp, i64, vp, sz, vp]),
         "fht_workspace_size_sheared": (i, [i, i, i, i, i, ctypes.POINTER(sz)]),
+        "fht_segment": (i, [i, i, i, i, i, i, i, ip, ip, ip, ip, ip]),
+        "fht_row_argmax": (i, [vp, i, i, i, i64, vp, vp, vp]),
         "fht_forward_sheared": (i, [vp, i, i, i, i64, i, d, i, i, vp, i, i64, vp, sz, vp]),
         "fht_shear_range": (i, [d, d, i, i, ip, ctypes.POINTER(d), ip, ip]),
         "fht_plan_create_batched": (i, [ctypes.POINTER(i), ctypes.POINTER(i), i, i, i, i,
@@ -273,6 +275,31 @@ def adjoint(grad: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: in
 
 
 # ------------------------------------------------------------------ batched
+
+# ------------------------------------------------------------------ back to lines
+
+def segment(h: int, w: int, row: int, col: int, layout: int = LAYOUT_FULL, q: int = Q0,
+            shifted: bool = False):
+    """The image segment Hough point (row, col) sums (Section 3.2):
+    (count, (r0, c0), (r1, c1)), or None when it lies wholly in the padding."""
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(lib.fht_segment(h, w, layout, q, row, col, int(shifted),
+                           *[ctypes.byref(x) for x in v]), "fht_segment")
+    if v[0].value == 0:
+        return None
+    return v[0].value, (v[1].value, v[2].value), (v[3].value, v[4].value)
+
+
+def row_argmax(hough: torch.Tensor, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+    """(max, first argmax) of every row of a 2-D int32/float32 CUDA tensor."""
+    code, pitch = _dev2d(hough, "hough")
+    rows, cols = hough.shape
+    vals = torch.empty(rows, dtype=hough.dtype, device=hough.device)
+    idx = torch.empty(rows, dtype=torch.int32, device=hough.device)
+    _check(lib.fht_row_argmax(_ptr(hough), code, rows, cols, pitch, _ptr(vals), _ptr(idx),
+                              _stream(stream)), "fht_row_argmax")
+    return vals, idx
+
 
 # ------------------------------------------------------------------ sheared (Section 4)
 

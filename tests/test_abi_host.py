@@ -9,7 +9,10 @@ import re
 import pytest
 import torch
 
+import numpy as np
+
 import oracle as O
+from workloads import random_image
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -178,3 +181,66 @@ def test_sheared_bad_arguments_rejected_on_host(fht):
     assert L.fht_workspace_size_sheared(4096, 4096, 0, I32, I32, ctypes.byref(n)) == 0
     assert n.value == 4096 * 8192 * 4
     assert L.fht_workspace_size_sheared(4096, 4096, 4, U8, I32, ctypes.byref(n)) == EINVAL
+
+
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
+@pytest.mark.parametrize("hw", [(9, 14), (16, 5), (1, 1), (33, 20)])
+def test_segment_matches_oracle(fht, q, hw):
+    """fht_segment (host) against the oracle's point -> segment on every point
+    of the quadrant."""
+    h, w = hw
+    n, W = O.quadrant_geometry(h, w, q)
+    for t in range(n):
+        for x in range(W):
+            assert fht.segment(h, w, t, x, fht.LAYOUT_QUADRANT, q) == \
+                O.point_segment(h, w, q, t, x), (t, x)
+
+
+@pytest.mark.parametrize("hw", [(9, 14), (5, 3), (12, 20)])
+def test_segment_full_layout_and_fhtshift(fht, hw):
+    """Full layout: the count is the full transform of an all-ones image at the
+    point (also after fhtshift, with shifted=1), and the run's pixel sum the
+    full transform of a random image."""
+    h, w = hw
+    ones = O.full(np.ones((h, w), np.uint8))
+    ones_s = O.fhtshift_full(ones, h, w)
+    img = random_image(h, w, "u8", seed=h)
+    F = O.full(img)
+    R, W = O.full_geometry(h, w)
+    rowmap = O.full_row_map(h, w)
+    hp, wp = O.next_pow2(h), O.next_pow2(w)
+    for r in range(R):
+        q, t = rowmap[r]
+        n = hp if q < 2 else wp
+        for x in range(W):
+            seg = fht.segment(h, w, r, x)
+            cnt = 0 if seg is None else seg[0]
+            assert cnt == ones[r, x], (r, x)
+            segs = fht.segment(h, w, r, x, shifted=True)
+            assert (0 if segs is None else segs[0]) == ones_s[r, x], (r, x)
+            if seg is None:
+                assert F[r, x] == 0
+                continue
+            _, a, b = seg
+            tr = q >= 2
+            ya, yb = (a[1], b[1]) if tr else (a[0], b[0])
+            tot = 0
+            for y in range(ya, yb + 1):
+                c = (x + O.SIGMA[q] * O.offset(n, t, y)) % W
+                rr, cc = (c, y) if tr else (y, c)
+                tot += int(img[rr, cc])
+            assert tot == F[r, x], (r, x)
+
+
+def test_segment_bad_arguments(fht):
+    L = fht.lib
+    v = [ctypes.c_int() for _ in range(5)]
+    refs = [ctypes.byref(x) for x in v]
+    assert L.fht_segment(8, 8, 0, 0, 8, 0, 0, *refs) == EINVAL      # t >= n
+    assert L.fht_segment(8, 8, 0, 0, 0, 16, 0, *refs) == EINVAL     # col >= W
+    assert L.fht_segment(8, 8, 1, 0, 29, 0, 0, *refs) == EINVAL     # full row out of range
+    assert L.fht_segment(8, 8, 0, 4, 0, 0, 0, *refs) == EINVAL      # quadrant
+    assert L.fht_row_argmax(ctypes.c_void_p(0x1000), 0, 4, 4, 4, ctypes.c_void_p(0x1000),
+                            ctypes.c_void_p(0x1000), ctypes.c_void_p(0)) == EINVAL  # u8
+    assert L.fht_row_argmax(ctypes.c_void_p(0x1000), 1, 4, 4, 3, ctypes.c_void_p(0x1000),
+                            ctypes.c_void_p(0x1000), ctypes.c_void_p(0)) == EINVAL  # pitch
