@@ -19,6 +19,7 @@ What is computed (Aliev, Ershov, Nikolaev, arXiv:1811.06378):
 * ``fhtshift``     per-row cyclic regrouping around the accumulator centre
                    (Section 5).
 * ``point_segment`` the image pixels one Hough point sums (Section 3.2).
+* ``quadrant_op``  maximum or minimum along the patterns instead of the sum.
 * ``sheared_quadrant`` the quadrant of the sheared image (Section 4).
 * ``adjoint_*``    the transpose of each map (not in the paper; defined by the
                    transform being linear), computed as the opposite-sign
@@ -102,6 +103,9 @@ def _load():
                          "fo_adjoint_i64", "fo_adjoint_f32", "fo_adjoint_f64"):
                 getattr(lib, name).restype = i
                 getattr(lib, name).argtypes = [p, i, i, i]
+            for name in ("fo_butterfly_op_i64", "fo_butterfly_op_f32"):
+                getattr(lib, name).restype = i
+                getattr(lib, name).argtypes = [p, i, i, i, i]
             lib.fo_points.restype = None
             lib.fo_points.argtypes = [p, i, i, i, i64, i, i, i, i, i, p, p, p]
             _lib = lib
@@ -139,6 +143,22 @@ def butterfly(P: np.ndarray, sigma: int, kind: str = "i64") -> np.ndarray:
     A = np.ascontiguousarray(P, dtype=dt).copy()
     n, W = A.shape
     if getattr(_load(), f"fo_butterfly_{kind}")(_ptr(A), n, W, sigma) != 0:
+        raise MemoryError("oracle butterfly scratch allocation failed")
+    return A
+
+
+OP_SUM, OP_MAX, OP_MIN = 0, 1, 2
+
+
+def butterfly_op(P: np.ndarray, sigma: int, op: int, kind: str = "i64") -> np.ndarray:
+    """The butterfly with maximum (op 1) or minimum (op 2) in place of the
+    sum; op 0 is the sum."""
+    if op == OP_SUM:
+        return butterfly(P, sigma, kind)
+    dt, _ = _CT[kind]
+    A = np.ascontiguousarray(P, dtype=dt).copy()
+    n, W = A.shape
+    if getattr(_load(), f"fo_butterfly_op_{kind}")(_ptr(A), n, W, sigma, op) != 0:
         raise MemoryError("oracle butterfly scratch allocation failed")
     return A
 
@@ -230,6 +250,17 @@ def quadrant(img: np.ndarray, q: int, kind: str = "i64") -> np.ndarray:
     src = img.T if TRANSPOSED[q] else img
     n, W = quadrant_geometry(img.shape[0], img.shape[1], q)
     return butterfly(padded(src, n, W, kind), SIGMA[q], kind)
+
+
+def quadrant_op(img: np.ndarray, q: int, op: int, kind: str = "i64") -> np.ndarray:
+    """Quadrant q with the maximum (op 1) or minimum (op 2) along every
+    pattern instead of the sum (the generalisation to associative-commutative
+    operations of the introduction); the padding stays zero (Section 3.1),
+    so a pattern that leaves the image takes zeros into its maximum or
+    minimum."""
+    src = img.T if TRANSPOSED[q] else img
+    n, W = quadrant_geometry(img.shape[0], img.shape[1], q)
+    return butterfly_op(padded(src, n, W, kind), SIGMA[q], op, kind)
 
 
 def _full_quadrants(img: np.ndarray, kind: str) -> dict[int, np.ndarray]:

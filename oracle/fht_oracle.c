@@ -113,6 +113,36 @@ DEFINE_BUTTERFLY(int64_t, fo_butterfly_i64)
 DEFINE_BUTTERFLY(float, fo_butterfly_f32)
 DEFINE_BUTTERFLY(double, fo_butterfly_f64)
 
+/* The same recursion with another associative-commutative operation in
+ * place of the sum (the paper's introduction: Hough transforms generalise to
+ * any such operation): op 1 = maximum, 2 = minimum, each level taking
+ * op(top[x], bot[x + sigma*ceil(t/2)]) as "top > bot ? top : bot" (max) or
+ * "top < bot ? top : bot" (min). The padding stays zero (Section 3.1). */
+#define DEFINE_BUTTERFLY_OP(T, NAME)                                            \
+    int NAME(T *A, int n, int W, int sigma, int op) {                           \
+        size_t bytes = (size_t)n * (size_t)W * sizeof(T);                       \
+        T *B = (T *)malloc(bytes ? bytes : 1);                                  \
+        if (!B) return -1;                                                      \
+        for (int half = 1; half < n; half *= 2) {                               \
+            for (int s0 = 0; s0 < n; s0 += 2 * half)                            \
+                for (int t = 0; t < 2 * half; ++t) {                            \
+                    const T *top = A + (int64_t)(s0 + t / 2) * W;               \
+                    const T *bot = A + (int64_t)(s0 + half + t / 2) * W;        \
+                    int64_t d = (int64_t)sigma * ((t + 1) / 2);                 \
+                    T *out = B + (int64_t)(s0 + t) * W;                         \
+                    for (int x = 0; x < W; ++x) {                               \
+                        T a = top[x], b = bot[wrap(x + d, W)];                  \
+                        out[x] = op == 1 ? (a > b ? a : b) : (a < b ? a : b);   \
+                    }                                                           \
+                }                                                               \
+            memcpy(A, B, bytes);                                                \
+        }                                                                       \
+        free(B);                                                                \
+        return 0;                                                               \
+    }
+DEFINE_BUTTERFLY_OP(int64_t, fo_butterfly_op_i64)
+DEFINE_BUTTERFLY_OP(float, fo_butterfly_op_f32)
+
 /* Transposed butterfly (adjoint), in place on A: levels in reverse order. In a
  * strip of 2*half rows, output slopes 2u and 2u+1 both read top row u at
  * column x and bottom row u at x + sigma*u and x + sigma*(u+1) respectively, so

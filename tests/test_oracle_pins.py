@@ -578,3 +578,46 @@ def test_point_segment_paper_cases():
     assert O.point_segment(h, w, 0, 7, 15) == (3, (3, 0), (5, 2))
     # vertical pattern in the extension (c)
     assert O.point_segment(h, w, 0, 0, 12) is None
+
+
+# --------------------------------------------------------------- other operations (max, min)
+
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
+@pytest.mark.parametrize("op", [1, 2])
+def test_max_min_equal_brute_force(q, op):
+    """Every point is the maximum (minimum) of the zero-padded image along the
+    pattern, written out with the closed-form offsets."""
+    img = random_image(7, 11, "u8", seed=q + 10 * op)
+    h, w = img.shape
+    src = img.T if O.TRANSPOSED[q] else img
+    n, W = O.quadrant_geometry(h, w, q)
+    P = np.zeros((n, W), np.int64)
+    P[:src.shape[0], :src.shape[1]] = src
+    f = max if op == 1 else min
+    H = np.array([[f(int(P[y, (x + O.SIGMA[q] * O.offset(n, t, y)) % W]) for y in range(n))
+                   for x in range(W)] for t in range(n)])
+    assert (O.quadrant_op(img, q, op) == H).all()
+
+
+@pytest.mark.parametrize("hw", [(16, 16), (13, 40), (64, 9)])
+def test_max_min_of_binary_images_follow_the_sum(hw):
+    """On a 0/1 image the maximum along a pattern is 1 exactly where the sum
+    is positive; on an all-ones image the minimum is 1 exactly where the
+    pattern never leaves the image (sum = n)."""
+    h, w = hw
+    img = (random_image(h, w, "u8", seed=h) > 200).astype(np.uint8)
+    for q in range(4):
+        assert (O.quadrant_op(img, q, 1) == (O.quadrant(img, q) > 0)).all()
+        ones = np.ones((h, w), np.uint8)
+        n, _ = O.quadrant_geometry(h, w, q)
+        assert (O.quadrant_op(ones, q, 2) == (O.quadrant(ones, q) == n)).all()
+
+
+def test_min_is_negated_max_of_negated_image():
+    """min along a pattern = -max of the negated values (zero padding is its
+    own negation), in int64 and in float32."""
+    img = random_image(20, 33, "i32", seed=4, hi=100)
+    for q in range(4):
+        assert (O.quadrant_op(img, q, 2) == -O.quadrant_op(-img, q, 1)).all()
+        f = img.astype(np.float32) / 7
+        assert (O.quadrant_op(f, q, 2, "f32") == -O.quadrant_op(-f, q, 1, "f32")).all()
