@@ -194,6 +194,27 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
                        void *grad_img, int64_t out_pitch, void *workspace,
                        size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------ other operations
+ * Hough transforms generalise to any associative-commutative operation along
+ * the lines (the paper's introduction). The same recursion with the maximum
+ * or the minimum in place of the sum: each level takes op(top, shifted
+ * bottom). The padding is the zero-filled extension of Section 3.1 for every
+ * operation, so a pattern that leaves the image takes zeros into its maximum
+ * or minimum. */
+typedef enum { FHT_OP_SUM = 0, FHT_OP_MAX = 1, FHT_OP_MIN = 2 } fht_op;
+
+/* Slope rows t_lo..t_hi of quadrant q with operation op, layout and
+ * arguments as fht_forward_range (op FHT_OP_SUM is fht_forward_range).
+ * FHT_OP_MAX / FHT_OP_MIN take uint8 -> int32 (uint16 intermediate levels) or
+ * float32 -> float32, else FHT_EUNSUPPORTED; the workspace
+ * fht_workspace_size gives for the same types is enough. Exact for integers;
+ * float32 maxima and minima are exact too (each result is one of the
+ * inputs or zero). */
+fht_status fht_forward_op(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                          fht_quadrant q, fht_op op, int t_lo, int t_hi, void *out,
+                          fht_dtype acc_t, int64_t out_pitch, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------------------ back to lines
  * Host only: the image segment that Hough point (row, col) sums (Section 3.2).
  * The point's pattern (the dyadic digital line of its slope, from its column)

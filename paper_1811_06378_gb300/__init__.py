@@ -67,6 +67,7 @@ def _load() -> ctypes.CDLL:
         "fht_adjoint": (i, [vp, i, i, i, i, i, i64, vp, i64, vp, sz, vp]),
         "fht_workspace_size_sheared": (i, [i, i, i, i, i, ctypes.POINTER(sz)]),
         "fht_segment": (i, [i, i, i, i, i, i, i, ip, ip, ip, ip, ip]),
+        "fht_forward_op": (i, [vp, i, i, i, i64, i, i, i, i, vp, i, i64, vp, sz, vp]),
         "fht_row_argmax": (i, [vp, i, i, i, i64, vp, vp, vp]),
         "fht_forward_sheared": (i, [vp, i, i, i, i64, i, d, i, i, vp, i, i64, vp, sz, vp]),
         "fht_shear_range": (i, [d, d, i, i, ip, ctypes.POINTER(d), ip, ip]),
@@ -275,6 +276,33 @@ def adjoint(grad: torch.Tensor, h: int, w: int, layout: int = LAYOUT_FULL, q: in
 
 
 # ------------------------------------------------------------------ batched
+
+# ------------------------------------------------------------------ other operations
+
+OP_SUM, OP_MAX, OP_MIN = 0, 1, 2
+
+
+def forward_op(img: torch.Tensor, q: int, op: int, t_lo: int = 0, t_hi: int | None = None,
+               acc: torch.dtype | None = None, out: torch.Tensor | None = None,
+               workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Slope rows t_lo..t_hi of quadrant q with the sum (OP_SUM), maximum
+    (OP_MAX) or minimum (OP_MIN) along every pattern (fht_forward_op)."""
+    it, ip = _dev2d(img, "img")
+    h, w = img.shape
+    n, W = query_shape(h, w, q)
+    t_hi = n - 1 if t_hi is None else t_hi
+    if acc is None:
+        acc = torch.float32 if img.dtype == torch.float32 else torch.int32
+    if out is None:
+        out = torch.empty((t_hi - t_lo + 1, W), dtype=acc, device=img.device)
+    _shape(out, (t_hi - t_lo + 1, W), "out")
+    ot, op_ = _dev2d(out, "out")
+    ws = _workspace(workspace, workspace_size(h, w, LAYOUT_QUADRANT, q, img.dtype, out.dtype),
+                    img.device)
+    _check(lib.fht_forward_op(_ptr(img), it, h, w, ip, q, op, t_lo, t_hi, _ptr(out), ot, op_,
+                              _ptr(ws), _nbytes(ws), _stream(stream)), "fht_forward_op")
+    return out
+
 
 # ------------------------------------------------------------------ back to lines
 

@@ -135,7 +135,7 @@ struct QuadPlan {
 // 4), also on cyclic full-width levels: the shear moves the black zone, so
 // the compact columns do not hold.
 QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
-                   bool adjoint = false, bool sheared = false) {
+                   bool adjoint = false, bool sheared = false, int op = 0) {
     QuadPlan P{};
     P.q = q;
     P.adjoint = adjoint;
@@ -168,6 +168,8 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
         int type = acc_elem;
         // u8 images summed over 2^k rows stay below 2^16 while k <= 8
         if (acc_elem == kI32 && in_elem == kU8 && k <= 8 && !adjoint) type = kU16;
+        // the maximum or minimum of uint8 values is one of them: uint16 at every level
+        if (acc_elem == kI32 && in_elem == kU8 && op != 0) type = kU16;
         P.lvl_type[p] = type;
         P.lvl_cols[p] = P.cyclic ? P.W : std::min(P.W, P.w_c + (1 << k));
         P.lvl_pitch[p] = (int64_t)align_up(P.lvl_cols[p], 64);
@@ -225,6 +227,20 @@ cudaError_t launch_forward(int M, const PassDesc &d, int acc, cudaStream_t st) {
     }
     if (src == kU16) return launch_fused_i32_u16(M, d, st);
     return launch_fused_i32_i32(M, d, st);
+}
+
+// The same for the maximum (op 1) or minimum (op 2) along the patterns:
+// uint8 images keep uint16 levels throughout.
+cudaError_t launch_forward_op(int M, const PassDesc &d, int acc, int op, cudaStream_t st) {
+    const int src = d.lo.type, dst = d.hi.type;
+    const bool mx = op == 1;
+    if (acc == kF32) return mx ? launch_max_f32(M, d, st) : launch_min_f32(M, d, st);
+    if (src == kU8) {
+        if (dst == kU16) return mx ? launch_max_i32_u8_u16(M, d, st) : launch_min_i32_u8_u16(M, d, st);
+        return mx ? launch_max_i32_u8_i32(M, d, st) : launch_min_i32_u8_i32(M, d, st);
+    }
+    if (dst == kU16) return mx ? launch_max_i32_u16_u16(M, d, st) : launch_min_i32_u16_u16(M, d, st);
+    return mx ? launch_max_i32_u16_i32(M, d, st) : launch_min_i32_u16_i32(M, d, st);
 }
 
 // Block-A warp-columns per tile: wider tiles compute less halo but need more
@@ -744,6 +760,40 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
         fht_status s = run_adjoint(P, gi, gh, full_map(qq, hp, wp), acc, qq > 0 ? 1 : 0,
                                    workspace, st);
         if (s != FHT_OK) return s;
+    }
+    return FHT_OK;
+}
+
+// ------------------------------------------------------------ other operations
+
+fht_status fht_forward_op(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                          fht_quadrant q, fht_op op, int t_lo, int t_hi, void *out,
+                          fht_dtype acc_t, int64_t out_pitch, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+    if (op == FHT_OP_SUM)
+        return forward_common(img, in_t, h, w, in_pitch, q, t_lo, t_hi, out, acc_t, out_pitch,
+                              workspace, workspace_bytes, stream);
+    if (op != FHT_OP_MAX && op != FHT_OP_MIN) return FHT_EINVAL;
+    if (!img || !out || !sizes_ok(h, w) || !quadrant_ok(q) || in_pitch < w) return FHT_EINVAL;
+    const int acc = acc_kind(in_t, acc_t);
+    if (acc < 0) return FHT_EINVAL;
+    const bool u8_i32 = in_t == FHT_U8 && acc_t == FHT_I32;
+    const bool f32_f32 = in_t == FHT_F32 && acc_t == FHT_F32;
+    if (!u8_i32 && !f32_f32) return FHT_EUNSUPPORTED;
+    QuadPlan P = make_plan(h, w, q, false, elem_of(in_t), acc, false, false, (int)op);
+    if (P.K > kMaxK) return FHT_EINVAL;
+    if (t_lo < 0 || t_hi < t_lo || t_hi >= P.n || out_pitch < P.W) return FHT_EINVAL;
+    const size_t need = plan_workspace(P);
+    if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
+    Side image{const_cast<void *>(img), in_pitch, elem_of(in_t), P.h_c, P.w_c};
+    Side o{out, out_pitch, elem_of(acc_t), 0, P.W};
+    for (int p = 0; p < P.npass; ++p) {
+        PassDesc d = pass_desc(P, p, image, o, workspace, quadrant_map(t_lo, t_hi), t_lo, t_hi);
+        const cudaError_t e = launch_forward_op(P.m[p], d, acc, (int)op, (cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            g_last_cuda_error = (int)e;
+            return FHT_ECUDA;
+        }
     }
     return FHT_OK;
 }

@@ -236,7 +236,7 @@ __device__ __forceinline__ void store8(E *row, int lo, int cols, const Acc (&v)[
 // MR levels on 2^MR rows x 8 columns held by this lane; a bottom row's shifted
 // columns past this lane's 8 come from lane+1 (lane 31 receives lane 0's,
 // which only ever reaches lane 31's own discarded results).
-template <int MR, typename Acc>
+template <int MR, typename Acc, int OP = 0>
 __device__ __forceinline__ void reg_butterfly(Acc (&v)[1 << MR][kV]) {
     constexpr int R = 1 << MR;
 #pragma unroll
@@ -255,8 +255,8 @@ __device__ __forceinline__ void reg_butterfly(Acc (&v)[1 << MR][kV]) {
                 for (int k = 0; k < kV; ++k) {
                     Acc b0 = k + u < kV ? bot[k + u] : nb[k + u - kV];
                     Acc b1 = k + u + 1 < kV ? bot[k + u + 1] : nb[k + u + 1 - kV];
-                    nv[s0 + 2 * u][k] = Arith<Acc>::add(top[k], b0);
-                    nv[s0 + 2 * u + 1][k] = Arith<Acc>::add(top[k], b1);
+                    nv[s0 + 2 * u][k] = Combine<Acc, OP>::apply(top[k], b0);
+                    nv[s0 + 2 * u + 1][k] = Combine<Acc, OP>::apply(top[k], b1);
                 }
             }
         }
@@ -973,7 +973,8 @@ __device__ __forceinline__ ItemPos item_pos(const PassDesc &d, int T, int gy, in
 // Block A of a two-block item (MB > 0): warps warp, warp + nwarps, ... load
 // mini-strips of RA source rows, run MA levels in registers and write the
 // results to the shared tile sm (nothing to do for a black tile).
-template <int MA, int MB, int SG, bool ADJ, typename Acc, typename SrcE, typename MidE>
+template <int MA, int MB, int SG, bool ADJ, typename Acc, typename SrcE, typename MidE,
+          int OP = 0>
 __device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &G,
                                              const ItemPos &ip, MidE *sm, int warp, int nwarps,
                                              int lane) {
@@ -988,7 +989,7 @@ __device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &
         Acc v[RA][kV];
         load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, ip.S, ip.a, g * RA, ip.A_off, wc * kWarpValid,
                                              i0, v);
-        reg_butterfly<MA, Acc>(v);
+        reg_butterfly<MA, Acc, OP>(v);
         if (lane < kLanesValid) {
             const int pos = (8 + PAD) * (i0 >> 3);   // i0 is a multiple of 8
 #pragma unroll
@@ -1011,7 +1012,8 @@ __device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &
 // Block B of a two-block item: level-MA slope a2 of every mini-strip g, read
 // from the shared tile with the shear a2*g, MB more levels, then the
 // destination (zeros for a black tile, without reading the tile).
-template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename MidE, typename DstE>
+template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename MidE, typename DstE,
+          int OP = 0>
 __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &G,
                                              const ItemPos &ip, const MidE *sm, int warp,
                                              int nwarps, int lane) {
@@ -1050,7 +1052,7 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
                 for (int k = 0; k < kV; ++k)
                     v[g][k] = (Acc)(k + delta >= kV ? raw[k + PAD] : raw[k]);
             }
-            reg_butterfly<MB, Acc>(v);
+            reg_butterfly<MB, Acc, OP>(v);
         } else {
 #pragma unroll
             for (int r = 0; r < RB; ++r)
@@ -1078,9 +1080,10 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
 // gradient source, image-gradient destination) so the forward kernels carry
 // none of its code; FIN likewise selects the destination (0 an intermediate
 // level, 1 the caller's layout, 2 an adjoint's transposed image gradient), so
-// each kernel holds one store path.
+// each kernel holds one store path. OP is the operation along the patterns
+// (Combine: 0 the sum, 1 the maximum, 2 the minimum).
 template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
-          typename DstE>
+          typename DstE, int OP = 0>
 __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm) {
     constexpr int M = MA + MB, RA = 1 << MA;
     constexpr int PAD = TilePad<MidE>::kPad;
@@ -1098,7 +1101,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             if (!ip.black) {
                 load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, ip.S, ip.a, 0, ip.A_off,
                                                      item * kWarpValid, i0, v);
-                reg_butterfly<MA, Acc>(v);
+                reg_butterfly<MA, Acc, OP>(v);
             } else {
 #pragma unroll
                 for (int r = 0; r < RA; ++r)
@@ -1118,9 +1121,9 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             }
         }
     } else {
-        tile_block_a<MA, MB, SG, ADJ, Acc, SrcE, MidE>(d, G, ip, sm, warp, nwarps, lane);
+        tile_block_a<MA, MB, SG, ADJ, Acc, SrcE, MidE, OP>(d, G, ip, sm, warp, nwarps, lane);
         if (!ip.black) __syncthreads();   // black is the same for the whole CTA
-        tile_block_b<MA, MB, SG, ADJ, FIN, Acc, MidE, DstE>(d, G, ip, sm, warp, nwarps, lane);
+        tile_block_b<MA, MB, SG, ADJ, FIN, Acc, MidE, DstE, OP>(d, G, ip, sm, warp, nwarps, lane);
     }
 }
 

@@ -56,11 +56,11 @@ constexpr int fused_min_blocks() {
 }
 
 template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
-          typename DstE>
+          typename DstE, int OP = 0>
 __global__ void __launch_bounds__(kFusedWarps * 32, fused_min_blocks<MidE>())
     fused_forward_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused_forward_item<MA, MB, SG, false, FIN, Acc, SrcE, MidE, DstE>(
+    fused_forward_item<MA, MB, SG, false, FIN, Acc, SrcE, MidE, DstE, OP>(
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
 }
 
@@ -165,14 +165,14 @@ struct FinCases {
 };
 
 template <int MA, int MB, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
-          typename DstE>
+          typename DstE, int OP = 0>
 void (*fused_kernel_ptr(int sigma))(PassDesc) {
     if constexpr (ADJ) {
         return sigma > 0 ? fused_adjoint_kernel<MA, MB, 1, FIN, Acc, SrcE, MidE, DstE>
                          : fused_adjoint_kernel<MA, MB, -1, FIN, Acc, SrcE, MidE, DstE>;
     } else {
-        return sigma > 0 ? fused_forward_kernel<MA, MB, 1, FIN, Acc, SrcE, MidE, DstE>
-                         : fused_forward_kernel<MA, MB, -1, FIN, Acc, SrcE, MidE, DstE>;
+        return sigma > 0 ? fused_forward_kernel<MA, MB, 1, FIN, Acc, SrcE, MidE, DstE, OP>
+                         : fused_forward_kernel<MA, MB, -1, FIN, Acc, SrcE, MidE, DstE, OP>;
     }
 }
 
@@ -230,13 +230,15 @@ cudaError_t launch_pipe_t(PassDesc d, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE,
+          int OP = 0>
 cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
+    static_assert(OP == 0 || !ADJ, "max / min transforms have no adjoint");
     if (d.batch < 1 || d.batch > 65535) return cudaErrorInvalidValue;
-    if constexpr (!kBatchable<Acc, SrcE>) {
+    if constexpr (!kBatchable<Acc, SrcE> || OP != 0) {
         if (d.batch > 1) return cudaErrorNotSupported;
     }
-    if constexpr (MB > 0) {
+    if constexpr (MB > 0 && OP == 0) {
         if (pipe_enabled() && d.batch == 1) {
             const cudaError_t e = launch_pipe_t<MA, MB, ADJ, Acc, SrcE, MidE, DstE>(d, st);
             if (e != cudaErrorNotSupported) return e;
@@ -260,7 +262,7 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     void (*k)(PassDesc) = nullptr;
     const int fin = !d.hi_final ? 0 : (ADJ && d.dst_transpose ? 2 : 1);
     if (d.batch > 1) {
-        if constexpr (kBatchable<Acc, SrcE>) {
+        if constexpr (kBatchable<Acc, SrcE> && OP == 0) {
             if (fin == 0) k = batch_kernel_ptr<MA, MB, ADJ, 0, Acc, SrcE, MidE, DstE>(d.sigma);
             else if (fin == 1) k = batch_kernel_ptr<MA, MB, ADJ, 1, Acc, SrcE, MidE, DstE>(d.sigma);
             else if constexpr (ADJ) k = batch_kernel_ptr<MA, MB, ADJ, 2, Acc, SrcE, MidE, DstE>(d.sigma);
@@ -270,10 +272,11 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
             if constexpr (ADJ) {
                 if (d.dst_transpose) k = fused_kernel_ptr<MA, MB, ADJ, 2, Acc, SrcE, MidE, DstE>(d.sigma);
             }
-            if (!k) k = fused_kernel_ptr<MA, MB, ADJ, 1, Acc, SrcE, MidE, DstE>(d.sigma);
+            if (!k) k = fused_kernel_ptr<MA, MB, ADJ, 1, Acc, SrcE, MidE, DstE, OP>(d.sigma);
         }
     } else {
-        if constexpr (FC::kLevel) k = fused_kernel_ptr<MA, MB, ADJ, 0, Acc, SrcE, MidE, DstE>(d.sigma);
+        if constexpr (FC::kLevel)
+            k = fused_kernel_ptr<MA, MB, ADJ, 0, Acc, SrcE, MidE, DstE, OP>(d.sigma);
     }
     if (!k) return cudaErrorInvalidValue;   // a type combination no plan produces
     if (smem > 48 * 1024) {
@@ -284,8 +287,10 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     char name[64];
     snprintf(name, sizeof name, "%s_m%d_%s%s%s",
              d.shear_on ? "sheared_fused"
-             : ADJ                                   ? "adjoint_fused"
-                                                     : "forward_fused",
+             : ADJ      ? "adjoint_fused"
+             : OP == 1  ? "forward_max"
+             : OP == 2  ? "forward_min"
+                        : "forward_fused",
              MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "", d.batch > 1 ? "_batch" : "");
     LaunchScope scope(name, st,
                       d.batch * pass_alg_bytes(d, MA + MB, sizeof(SrcE), sizeof(DstE)));
@@ -294,16 +299,16 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
+template <bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE, int OP = 0>
 cudaError_t launch_fused_m(int M, const PassDesc &d, cudaStream_t st) {
     switch (M) {
-    case 0: return launch_fused_t<0, 0, ADJ, Acc, SrcE, MidE, DstE>(d, st);
-    case 1: return launch_fused_t<1, 0, ADJ, Acc, SrcE, MidE, DstE>(d, st);
-    case 2: return launch_fused_t<2, 0, ADJ, Acc, SrcE, MidE, DstE>(d, st);
-    case 3: return launch_fused_t<3, 0, ADJ, Acc, SrcE, MidE, DstE>(d, st);
-    case 4: return launch_fused_t<3, 1, ADJ, Acc, SrcE, MidE, DstE>(d, st);
-    case 5: return launch_fused_t<3, 2, ADJ, Acc, SrcE, MidE, DstE>(d, st);
-    default: return launch_fused_t<3, 3, ADJ, Acc, SrcE, MidE, DstE>(d, st);
+    case 0: return launch_fused_t<0, 0, ADJ, Acc, SrcE, MidE, DstE, OP>(d, st);
+    case 1: return launch_fused_t<1, 0, ADJ, Acc, SrcE, MidE, DstE, OP>(d, st);
+    case 2: return launch_fused_t<2, 0, ADJ, Acc, SrcE, MidE, DstE, OP>(d, st);
+    case 3: return launch_fused_t<3, 0, ADJ, Acc, SrcE, MidE, DstE, OP>(d, st);
+    case 4: return launch_fused_t<3, 1, ADJ, Acc, SrcE, MidE, DstE, OP>(d, st);
+    case 5: return launch_fused_t<3, 2, ADJ, Acc, SrcE, MidE, DstE, OP>(d, st);
+    default: return launch_fused_t<3, 3, ADJ, Acc, SrcE, MidE, DstE, OP>(d, st);
     }
 }
 

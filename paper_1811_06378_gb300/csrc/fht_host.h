@@ -77,5 +77,16 @@ cudaError_t launch_adjoint_f32_u8(int M, const PassDesc &d, cudaStream_t st);
 cudaError_t launch_adjoint_i32_u8(int M, const PassDesc &d, cudaStream_t st);
 cudaError_t launch_adjoint_i32_u8_u16(int M, const PassDesc &d, cudaStream_t st);
 cudaError_t launch_adjoint_i32_u16(int M, const PassDesc &d, cudaStream_t st);
+// Forward passes with the maximum / minimum along the patterns (OP 1 / 2).
+cudaError_t launch_max_i32_u8_u16(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_max_i32_u8_i32(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_max_i32_u16_u16(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_max_i32_u16_i32(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_max_f32(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_min_i32_u8_u16(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_min_i32_u8_i32(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_min_i32_u16_u16(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_min_i32_u16_i32(int M, const PassDesc &d, cudaStream_t st);
+cudaError_t launch_min_f32(int M, const PassDesc &d, cudaStream_t st);
 
 }  // namespace fht
