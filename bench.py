@@ -22,7 +22,10 @@ batched path are reported under "rows".
 
 Rows also include the batched path: 512 uint8 edge maps with sides
 log-uniform in [64, 1024] in one persistent launch, against one fht_forward
-call per image.
+call per image, and its FP32 adjoint the same way; the [-15, 15] degree range
+as one sheared quadrant (Section 4); the maximum along the patterns of Q0;
+the per-row maxima of the full image; one gradient step of the 64 x 1024^2
+reconstruction.
 
 Multi-GPU: replicas only (each rank transforms its own image, no collective
 on the data path); value sums all ranks, time is the max over ranks.
@@ -419,6 +422,42 @@ def run_ours(args):
         rows["batched_512_u8_q0"]["speedup_vs_per_image"] = (
             rows["per_image_512_u8_q0"]["ms"] / rows["batched_512_u8_q0"]["ms"])
         del bimgs, bouts, bws, plan
+        # batched adjoint: FP32 gradients of the same 512 quadrants back onto
+        # their images in one persistent launch, against one call per image
+        fplan = fht.BatchPlan(shapes, 0, torch.float32, torch.float32)
+        fws = fplan.workspace(dev)
+        g512 = [torch.randn(sh, generator=gen, device=dev) for sh in fplan.out_shapes]
+        gi512 = [torch.empty(sh, dtype=torch.float32, device=dev) for sh in shapes]
+        badj = sum(n * W * 4 for n, W in fplan.out_shapes) + bpix * 4
+        rows["batched_adjoint_512_f32_q0"] = row_entry(
+            lambda: fplan.adjoint(g512, gi512, fws), badj, bpix)
+        pws_f = torch.empty(max(fht.workspace_size(1024, 1024, fht.LAYOUT_QUADRANT, 0,
+                                                   torch.float32, torch.float32), 1),
+                            dtype=torch.uint8, device=dev)
+        rows["per_image_adjoint_512_f32_q0"] = row_entry(
+            lambda: [fht.adjoint(g, h, w, fht.LAYOUT_QUADRANT, 0, out=o, workspace=pws_f)
+                     for (h, w), g, o in zip(shapes, g512, gi512)], badj, bpix)
+        rows["batched_adjoint_512_f32_q0"]["speedup_vs_per_image"] = (
+            rows["per_image_adjoint_512_f32_q0"]["ms"] / rows["batched_adjoint_512_f32_q0"]["ms"])
+        del fplan, fws, g512, gi512
+        # Section 4: the [-15, 15] degree range as ONE sheared quadrant (the
+        # paper's shear in the first iteration), against the two pruned
+        # quadrants of the range row above
+        sq, spl, st0, st1 = fht.shear_range(*RANGE_DEG, S, S)
+        sh_out = torch.empty((st1 - st0 + 1, fht.query_shape(S, S, sq)[1]), dtype=torch.int32,
+                             device=dev)
+        sh_ws = torch.empty(fht.workspace_size_sheared(S, S, sq, torch.uint8, torch.int32),
+                            dtype=torch.uint8, device=dev)
+        rows["sheared_range_pm15deg_int32"] = row_entry(
+            lambda: fht.forward_sheared(img, sq, spl, st0, st1, out=sh_out, workspace=sh_ws),
+            S * S + sh_out.numel() * 4, S * S)
+        del sh_out, sh_ws
+        # other operations: the maximum along every pattern of Q0
+        rows["max_q0_int32"] = row_entry(
+            lambda: fht.forward_op(img, 0, fht.OP_MAX, out=H0, workspace=ws),
+            S * S + n0 * W0 * 4, S * S)
+        # back to lines: the strongest line of every slope of the full image
+        rows["row_argmax_full_int32"] = row_entry(lambda: fht.row_argmax(F), R * Wf * 4, S * S)
         # differentiable path: one gradient-descent step of the 64 x 1024^2 FP32
         # reconstruction (full-image forward + adjoint per image, plus the update)
         from workloads import ellipse_phantom
