@@ -950,6 +950,24 @@ __device__ __forceinline__ bool tile_all_black(const PassDesc &d, int M, int a, 
     return lo >= d.black_wc + t_max;
 }
 
+// Sheared forward, first pass: is the tile [p0, p0 + T) outside the content of
+// its strip S? The strip's image rows y (level k1 = M) are rotated by s(y),
+// monotone in y, so its level-k1 rows are zero outside the columns
+// [s_lo, s_hi + w + 2^k1] (cyclic; both signs' compact columns fall inside).
+__device__ __forceinline__ bool sheared_tile_zero(const PassDesc &d, int M, int S, int p0,
+                                                  int T) {
+    const int y0 = S << M;
+    int y1 = y0 + (1 << M) - 1;
+    if (y1 >= d.lo.rows) y1 = d.lo.rows - 1;
+    if (y1 < y0) return true;   // no image row in the strip
+    const int sa = shear_shift(d, y0), sb = shear_shift(d, y1);
+    const int lo = sa < sb ? sa : sb, hi = sa < sb ? sb : sa;
+    const int len = hi - lo + d.lo.cols + (1 << M) + 1;
+    if (len + T >= d.W) return false;
+    const int j = wrap_w(p0 - lo, d.W);
+    return !(j < len || j + T > d.W);
+}
+
 // Where one (group, tile) item of a pass sits: its group (S, a), first
 // output column p0, the buffer column offsets of its source (A_off) and
 // destination (D), and whether the whole tile is black (all zero).
@@ -966,7 +984,10 @@ __device__ __forceinline__ ItemPos item_pos(const PassDesc &d, int T, int gy, in
     ip.p0 = d.p_begin + tile * T;
     ip.A_off = SG > 0 ? ip.p0 - (1 << (d.k0 + M)) + (1 << d.k0) : ip.p0 + T - 1;
     ip.D = SG > 0 ? ip.p0 : ip.p0 + T - 1;
-    ip.black = !ADJ && FIN && tile_all_black(d, M, ip.a, ip.p0, T);
+    if constexpr (ADJ && !FIN)
+        ip.black = d.shear_on && d.lo_image && sheared_tile_zero(d, M, ip.S, ip.p0, T);
+    else
+        ip.black = !ADJ && FIN && tile_all_black(d, M, ip.a, ip.p0, T);
     return ip;
 }
 
