@@ -291,9 +291,11 @@ __host__ __device__ inline TileGeom tile_geom(int MA, int MB, int n_a, int nwarp
     g.n_a = n_a;
     g.tile_out = (n_a * kWarpValid - reach) / kV * kV;
     g.n_b = (g.tile_out + kWarpValid - 1) / kWarpValid;
-    // highest column block B loads (+1), lane 31 included, plus one granule
-    const int max_col = (g.n_b - 1) * kWarpValid + 32 * kV + (RA - 1) * (RB - 1) + kV;
-    g.cols = (max_col > n_a * kWarpValid ? max_col : n_a * kWarpValid + kV);
+    // highest column block B loads (+1): lanes past the tile read as the
+    // first lane past it (tile_block_b), which is the last one a stored
+    // lane takes shuffled columns from; one granule more for the pad
+    const int max_col = g.tile_out + (RA - 1) * (RB - 1) + kV + 1;
+    g.cols = (max_col > n_a * kWarpValid ? max_col : n_a * kWarpValid);
     g.cols = (g.cols + 7) & ~7;
     g.pitch = (tile_pos(g.cols, pad) + 7) & ~7;
     return g;
@@ -1059,11 +1061,14 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
             }
         }
         const int i0 = jc * kWarpValid + lane * kV;
+        // lanes past the tile store nothing: they read where the first of
+        // them reads, so the tile ends where that lane's columns end
+        const int i0r = i0 < T ? i0 : T;
         Acc v[RB][kV];
         if (!ip.black) {
 #pragma unroll
             for (int g = 0; g < RB; ++g) {
-                const int x0 = i0 + a2 * g;
+                const int x0 = i0r + a2 * g;
                 const int delta = x0 & 7;
                 const MidE *row = sm + (g * RA + a2) * P + tile_pos(x0, PAD);
                 MidE raw[kV + PAD];

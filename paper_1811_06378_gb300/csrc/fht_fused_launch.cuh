@@ -48,11 +48,15 @@ inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t 
 // SG is the pass's sign in buffer coordinates (+1 or -1) and FIN what it
 // writes (0 an intermediate level, 1 the final level, 2 the final level of
 // an adjoint into a transposed image gradient), both fixed at compile time.
-// CTAs per SM the register budget is sized for: three with a 2-byte shared
-// tile (its 51 KB fits three times), else two.
+// CTAs per SM the register budget is sized for: three (24 warps). A shared
+// tile ends at the last column a stored lane reads (tile_geom), so a 2-byte
+// tile (51 KB) or a 4-byte one of a 3 + 3-level pass (74 KB) fits three times.
+// For 4-byte passes the 80 registers this leaves cost a few spills; measured
+// at 4096^2, the final int32 pass still gains 2% over two CTAs at 120
+// registers.
 template <typename MidE>
 constexpr int fused_min_blocks() {
-    return sizeof(MidE) == 2 ? 24 / kFusedWarps : 16 / kFusedWarps;
+    return 24 / kFusedWarps;
 }
 
 template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
