@@ -188,6 +188,29 @@ def whole_job_mpix_s(world: int, pixels_per_rank_step: int, ms_per_step: float) 
     return world * pixels_per_rank_step / 1e6 / (ms_per_step / 1e3)
 
 
+def bind_near_gpu(index: int):
+    """Keep this process on the CPU cores local to GPU `index` (its sysfs
+    local_cpulist), so that the pinned host buffers of the end-to-end region
+    and the copies through them stay on the GPU's NUMA node. Best effort:
+    returns the cores used, or None when the topology is not readable."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(index)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+            return sorted(cpus)
+    except Exception:
+        return None
+    return None
+
+
 def dist_setup():
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -282,6 +305,7 @@ def run_ours(args):
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    near_cpus = bind_near_gpu(local)
     stream = torch.cuda.current_stream()
     S = args.side
 
@@ -382,11 +406,143 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = whole_job_mpix_s(world, S * S, ms_per_step)
     prof_total_ms = sum(prof_step_ms)
-
-    # ---- per-row measurements (same flush discipline)
     peak, peak_kind = load_peaks()
+    rows = {}   # filled by the per-row section below
+
+    # ---- roofline of the dominant kernel (largest share of the profiled
+    # step): the library's CUDA events on the launch stream give its launch
+    # times, and its algorithmic bytes per launch (the level it reads as
+    # stored plus the level it writes, from the launch geometry)
+    dom_name, (dom_launches, dom_ms, dom_bytes) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_ms = dom_ms / max(dom_launches, 1)
+    bytes_per_launch = dom_bytes / max(dom_launches, 1)
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    traffic = traffic_per_launch(dom_name, S)
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak, "traffic": traffic,
+        "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+        "kernel": dom_name, "launches_profiled": dom_launches,
+        "avg_launch_ms": avg_ms, "alg_bytes_per_launch": bytes_per_launch,
+        "share_of_step": dom_ms / prof_total_ms,
+    }
+    kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / max(v[0], 1),
+                   "alg_bytes_per_launch": v[2] / max(v[0], 1),
+                   "achieved_gbs": (v[2] / max(v[0], 1)) / (v[1] / max(v[0], 1) / 1e3) / 1e9,
+                   "share_of_step": v[1] / prof_total_ms} for k, v in prof.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{S}x{S} u8 edge map (5% edges + 4 lines): full "
+                               "4-quadrant image, fhtshift, [-15,15] deg range, FP32 "
+                               "full adjoint", "l2": "flushed before every timed step",
+                   "parallelism": f"replicas x{world}",
+                   "timing": "value: K replays of the step captured as one CUDA graph; "
+                             "roofline and kernels: a second region of the same K steps "
+                             "launched call by call with per-launch CUDA events",
+                   "profiled_ms_per_step": prof_total_ms / args.steps,
+                   "host_cores": (f"{len(near_cpus)} cores local to the GPU" if near_cpus
+                                  else "unbound"),
+                   "launches_per_step": launches_per_step},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "kernels": kernels,
+        "rows": rows,
+        "clocks": clk,
+    }
+
+    # ---- end to end through the public API with host buffers. Every step
+    # copies its own inputs (image, gradient) in from pinned host memory and
+    # its results (full image, fhtshift image, range slices, image gradient)
+    # out to pinned host memory. Three streams: host-to-device copies,
+    # compute, device-to-host copies; each result's copy starts as soon as
+    # its kernels are done, and the next step's inputs land in a second set of
+    # device buffers while the current step computes.
+    if not args.no_e2e:
+        img_pin = torch.from_numpy(img_h).pin_memory()
+        grad_pin = torch.empty((R, Wf), dtype=torch.float32).pin_memory()
+        grad_pin.copy_(grad.cpu())
+        host_out = {"F": torch.empty((R, Wf), dtype=torch.int32).pin_memory(),
+                    "Fs": torch.empty((R, Wf), dtype=torch.int32).pin_memory(),
+                    "g": torch.empty((S, S), dtype=torch.float32).pin_memory()}
+        host_out.update({f"r{q}": torch.empty(tuple(rng_out[q].shape), dtype=torch.int32)
+                         .pin_memory() for q in used})
+        bufs = []
+        for _ in range(2):
+            bufs.append({"img": torch.empty_like(img), "grad": torch.empty_like(grad),
+                         "F": torch.empty_like(F), "Fs": torch.empty_like(Fs),
+                         "g": torch.empty_like(gimg),
+                         **{f"r{q}": torch.empty_like(rng_out[q]) for q in used}})
+        s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        ev = lambda: torch.cuda.Event()   # noqa: E731
+        in_free = [None, None]    # compute of the buffer set's previous step is done
+        out_free = [None, None]   # device-to-host copies of its previous step are done
+
+        def e2e_step(i):
+            b = bufs[i % 2]
+            with torch.cuda.stream(s_in):
+                if in_free[i % 2] is not None:
+                    s_in.wait_event(in_free[i % 2])
+                b["img"].copy_(img_pin, non_blocking=True)
+                e_img = ev(); e_img.record(s_in)
+                b["grad"].copy_(grad_pin, non_blocking=True)
+                e_grad = ev(); e_grad.record(s_in)
+            if out_free[i % 2] is not None:
+                s_cmp.wait_event(out_free[i % 2])
+            s_cmp.wait_event(e_img)
+            fht.full_quadrants(b["img"], out=b["F"], workspace=ws, stream=s_cmp)
+            e_f = ev(); e_f.record(s_cmp)
+            fht.fhtshift(b["F"], S, S, fht.LAYOUT_FULL, out=b["Fs"], stream=s_cmp)
+            e_fs = ev(); e_fs.record(s_cmp)
+            for q in used:
+                fht.forward_range(b["img"], q, lo[q], hi[q], out=b[f"r{q}"], workspace=ws,
+                                  stream=s_cmp)
+            e_r = ev(); e_r.record(s_cmp)
+            s_cmp.wait_event(e_grad)
+            fht.adjoint(b["grad"], S, S, fht.LAYOUT_FULL, out=b["g"], workspace=ws,
+                        stream=s_cmp)
+            e_g = ev(); e_g.record(s_cmp)
+            in_free[i % 2] = e_g
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(e_f)
+                host_out["F"].copy_(b["F"], non_blocking=True)
+                s_out.wait_event(e_fs)
+                host_out["Fs"].copy_(b["Fs"], non_blocking=True)
+                s_out.wait_event(e_r)
+                for q in used:
+                    host_out[f"r{q}"].copy_(b[f"r{q}"], non_blocking=True)
+                s_out.wait_event(e_g)
+                host_out["g"].copy_(b["g"], non_blocking=True)
+                done = ev(); done.record(s_out)
+            out_free[i % 2] = done
+
+        for i in range(2):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        k = max(3, min(args.steps, 20))
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(s_in)
+        for i in range(k):
+            e2e_step(i)
+        t1.record(s_out)
+        torch.cuda.synchronize()
+        e_ms = t0.elapsed_time(t1) / k
+        h2d = img.numel() + grad.numel() * 4
+        d2h = sum(t.numel() * t.element_size() for t in host_out.values())
+        line["e2e"] = {"value": world * S * S / 1e6 / (e_ms / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "ms_per_step": e_ms, "steps": k,
+                       "streams": "host-to-device, compute and device-to-host copies "
+                                  "on three streams, two device buffer sets"}
+        del bufs
+
+    # ---- per-row measurements (same flush discipline), after the end-to-end
+    # region: their host-side loops and allocations come after its copies
     reps = max(10, min(args.steps, 50))
-    rows = {}
     if not args.no_rows:
         def row_entry(fn, alg_bytes, pixels):
             t = statistics.median(timed(fn, reps))
@@ -488,135 +644,6 @@ def run_ours(args):
         torch.cuda.synchronize()
         rows["gd_step_64x1024_f32"] = row_entry(gd_graph.replay, gd_alg, B5 * n5 * n5)
         del xt, b5, x5, gd_graph
-
-    # ---- roofline of the dominant kernel (largest share of the profiled
-    # step): the library's CUDA events on the launch stream give its launch
-    # times, and its algorithmic bytes per launch (the level it reads as
-    # stored plus the level it writes, from the launch geometry)
-    dom_name, (dom_launches, dom_ms, dom_bytes) = max(prof.items(), key=lambda kv: kv[1][1])
-    avg_ms = dom_ms / max(dom_launches, 1)
-    bytes_per_launch = dom_bytes / max(dom_launches, 1)
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    traffic = traffic_per_launch(dom_name, S)
-    roofline = {
-        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-        "frac": achieved / peak, "traffic": traffic,
-        "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-        "kernel": dom_name, "launches_profiled": dom_launches,
-        "avg_launch_ms": avg_ms, "alg_bytes_per_launch": bytes_per_launch,
-        "share_of_step": dom_ms / prof_total_ms,
-    }
-    kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / max(v[0], 1),
-                   "alg_bytes_per_launch": v[2] / max(v[0], 1),
-                   "achieved_gbs": (v[2] / max(v[0], 1)) / (v[1] / max(v[0], 1) / 1e3) / 1e9,
-                   "share_of_step": v[1] / prof_total_ms} for k, v in prof.items()}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"{S}x{S} u8 edge map (5% edges + 4 lines): full "
-                               "4-quadrant image, fhtshift, [-15,15] deg range, FP32 "
-                               "full adjoint", "l2": "flushed before every timed step",
-                   "parallelism": f"replicas x{world}",
-                   "timing": "value: K replays of the step captured as one CUDA graph; "
-                             "roofline and kernels: a second region of the same K steps "
-                             "launched call by call with per-launch CUDA events",
-                   "profiled_ms_per_step": prof_total_ms / args.steps,
-                   "launches_per_step": launches_per_step},
-        "roofline": roofline,
-        "gpu_launches": launches,
-        "kernels": kernels,
-        "rows": rows,
-        "clocks": clk,
-    }
-
-    # ---- end to end through the public API with host buffers. Every step
-    # copies its own inputs (image, gradient) in from pinned host memory and
-    # its results (full image, fhtshift image, range slices, image gradient)
-    # out to pinned host memory. Three streams: host-to-device copies,
-    # compute, device-to-host copies; each result's copy starts as soon as
-    # its kernels are done, and the next step's inputs land in a second set of
-    # device buffers while the current step computes.
-    if not args.no_e2e:
-        img_pin = torch.from_numpy(img_h).pin_memory()
-        grad_pin = torch.empty((R, Wf), dtype=torch.float32).pin_memory()
-        grad_pin.copy_(grad.cpu())
-        host_out = {"F": torch.empty((R, Wf), dtype=torch.int32).pin_memory(),
-                    "Fs": torch.empty((R, Wf), dtype=torch.int32).pin_memory(),
-                    "g": torch.empty((S, S), dtype=torch.float32).pin_memory()}
-        host_out.update({f"r{q}": torch.empty(tuple(rng_out[q].shape), dtype=torch.int32)
-                         .pin_memory() for q in used})
-        bufs = []
-        for _ in range(2):
-            bufs.append({"img": torch.empty_like(img), "grad": torch.empty_like(grad),
-                         "F": torch.empty_like(F), "Fs": torch.empty_like(Fs),
-                         "g": torch.empty_like(gimg),
-                         **{f"r{q}": torch.empty_like(rng_out[q]) for q in used}})
-        s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        ev = lambda: torch.cuda.Event()   # noqa: E731
-        in_free = [None, None]    # compute of the buffer set's previous step is done
-        out_free = [None, None]   # device-to-host copies of its previous step are done
-
-        def e2e_step(i):
-            b = bufs[i % 2]
-            with torch.cuda.stream(s_in):
-                if in_free[i % 2] is not None:
-                    s_in.wait_event(in_free[i % 2])
-                b["img"].copy_(img_pin, non_blocking=True)
-                e_img = ev(); e_img.record(s_in)
-                b["grad"].copy_(grad_pin, non_blocking=True)
-                e_grad = ev(); e_grad.record(s_in)
-            if out_free[i % 2] is not None:
-                s_cmp.wait_event(out_free[i % 2])
-            s_cmp.wait_event(e_img)
-            fht.full_quadrants(b["img"], out=b["F"], workspace=ws, stream=s_cmp)
-            e_f = ev(); e_f.record(s_cmp)
-            fht.fhtshift(b["F"], S, S, fht.LAYOUT_FULL, out=b["Fs"], stream=s_cmp)
-            e_fs = ev(); e_fs.record(s_cmp)
-            for q in used:
-                fht.forward_range(b["img"], q, lo[q], hi[q], out=b[f"r{q}"], workspace=ws,
-                                  stream=s_cmp)
-            e_r = ev(); e_r.record(s_cmp)
-            s_cmp.wait_event(e_grad)
-            fht.adjoint(b["grad"], S, S, fht.LAYOUT_FULL, out=b["g"], workspace=ws,
-                        stream=s_cmp)
-            e_g = ev(); e_g.record(s_cmp)
-            in_free[i % 2] = e_g
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(e_f)
-                host_out["F"].copy_(b["F"], non_blocking=True)
-                s_out.wait_event(e_fs)
-                host_out["Fs"].copy_(b["Fs"], non_blocking=True)
-                s_out.wait_event(e_r)
-                for q in used:
-                    host_out[f"r{q}"].copy_(b[f"r{q}"], non_blocking=True)
-                s_out.wait_event(e_g)
-                host_out["g"].copy_(b["g"], non_blocking=True)
-                done = ev(); done.record(s_out)
-            out_free[i % 2] = done
-
-        for i in range(2):
-            e2e_step(i)
-        torch.cuda.synchronize()
-        k = max(3, min(args.steps, 20))
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(s_in)
-        for i in range(k):
-            e2e_step(i)
-        t1.record(s_out)
-        torch.cuda.synchronize()
-        e_ms = t0.elapsed_time(t1) / k
-        h2d = img.numel() + grad.numel() * 4
-        d2h = sum(t.numel() * t.element_size() for t in host_out.values())
-        line["e2e"] = {"value": world * S * S / 1e6 / (e_ms / 1e3), "unit": UNIT,
-                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                       "ms_per_step": e_ms, "steps": k,
-                       "streams": "host-to-device, compute and device-to-host copies "
-                                  "on three streams, two device buffer sets"}
-        del bufs
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(S)

@@ -318,6 +318,32 @@ def test_config_4096_all_quadrants_sampled(fht):
         assert (F[rows[sel], cols[sel]] == vals).all(), q
 
 
+def test_bench_step_4096_complete(fht):
+    """The benchmark's step on its own image and in its own calls (one shared
+    workspace, the fused-range calls of the step): the 16381 x 8192 full Hough
+    image, its fhtshift and the [-15, 15] degree slope rows of Q0 and Q1, every
+    element against the oracle (the step's FP32 adjoint is checked complete by
+    test_adjoint_full_4096_complete)."""
+    S = 4096
+    img = edges_and_lines(S, S, p_edge=0.05, n_lines=4, seed=4096)
+    x = dev(img)
+    ws = torch.empty(max(fht.workspace_size(S, S, fht.LAYOUT_FULL, 0, torch.uint8, torch.int32),
+                         fht.workspace_size(S, S, fht.LAYOUT_QUADRANT, 1, torch.uint8,
+                                            torch.int32)), dtype=torch.uint8, device="cuda")
+    F = fht.full_quadrants(x, workspace=ws)
+    Fs = fht.fhtshift(F, S, S, fht.LAYOUT_FULL)
+    lo, hi = fht.angle_to_slopes(-15.0, 15.0, S, S)
+    assert (lo[0], hi[0], lo[1], hi[1]) == (0, 1097, 1, 1097)
+    rng_rows = {q: host(fht.forward_range(x, q, lo[q], hi[q], workspace=ws)) for q in (0, 1)}
+    want_F = O.full(img)
+    assert (host(F) == want_F).all()
+    assert (host(Fs) == O.fhtshift_full(want_F, S, S)).all()
+    for q in (0, 1):
+        assert (rng_rows[q] == O.range_slice(img, q, lo[q], hi[q])).all(), q
+    del F, Fs, ws
+    torch.cuda.empty_cache()
+
+
 def test_config_8192_f32_sampled_and_tree(fht):
     """8192 x 8192 FP32 ellipse phantom: Q0 bit-exact against the FP32 tree,
     all four quadrants within 1e-5 * sum|I| of FP64 brute force at sampled
