@@ -100,3 +100,23 @@ def test_sheared_three_passes(fht):
         got = host(fht.forward_sheared(x, q, spl, 1000, 2999))
         want = O.sheared_quadrant(img, q, spl, t_lo=1000, t_hi=2999)
         assert (got == as_i32(want)).all(), q
+
+
+def test_sheared_and_ops_on_unaligned_views(fht):
+    """Images that start at odd element offsets inside a wider buffer (odd
+    pitch, unaligned rows): the sheared transform and the maximum still match
+    the oracle exactly, so the vector fast paths and the edge paths agree."""
+    h, w = 150, 203
+    rng = np.random.default_rng(17)
+    big = rng.integers(0, 256, size=(h + 3, w + 37)).astype(np.uint8)
+    view = torch.from_numpy(big).cuda()[1:1 + h, 5:5 + w]      # pitch w + 37, offset 1 row + 5
+    img = big[1:1 + h, 5:5 + w]
+    for q, spl in ((0, 0.3), (2, -0.7)):
+        got = fht.forward_sheared(view, q, spl).cpu().numpy()
+        assert (got == as_i32(O.sheared_quadrant(img, q, spl))).all(), q
+    got = fht.forward_op(view, 1, 1).cpu().numpy()
+    assert (got == O.quadrant_op(img, 1, 1)).all()
+    bigf = rng.standard_normal((h + 2, w + 9)).astype(np.float32)
+    vf = torch.from_numpy(bigf).cuda()[2:2 + h, 3:3 + w]
+    got = fht.forward_op(vf, 3, 2).cpu().numpy()
+    assert (got == O.quadrant_op(bigf[2:2 + h, 3:3 + w], 3, 2, "f32")).all()
