@@ -253,6 +253,7 @@ struct Tune {
     int n_a_u16 = 1;    // first pass over uint8 images (uint16 shared tile)
     int n_a_wide = 1;   // 4-byte shared tiles
     bool pipe = false;
+    bool staged = true;
     Tune() {
         if (const char *e = getenv("FHT_TUNE")) {
             int a = 0, b = 0;
@@ -262,6 +263,7 @@ struct Tune {
             }
         }
         if (const char *e = getenv("FHT_PIPE")) pipe = e[0] == '1' && e[1] == 0;
+        if (const char *e = getenv("FHT_STAGED")) staged = !(e[0] == '0' && e[1] == 0);
     }
 };
 const Tune g_tune;
@@ -280,6 +282,7 @@ std::vector<unsigned int (*)()> &counter_fns() {
 namespace fht {
 
 bool pipe_enabled() { return g_tune.pipe; }
+bool staged_enabled() { return g_tune.staged; }
 
 bool register_device_counter(unsigned int (*read_and_reset)()) {
     std::lock_guard<std::mutex> lk(counter_mu());

@@ -9,6 +9,7 @@
 #include "fht_fused.cuh"
 #include "fht_host.h"
 #include "fht_pipe.cuh"
+#include "fht_staged.cuh"
 
 namespace fht {
 
@@ -234,6 +235,37 @@ cudaError_t launch_pipe_t(PassDesc d, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// The staged persistent form of the final pass from a uint16 level
+// (fht_staged.cuh): grid = SMs x resident CTAs, items taken in turn.
+template <typename Dummy = void>
+cudaError_t launch_staged(PassDesc d, cudaStream_t st) {
+    const TileGeom G = tile_geom(3, 3, 1, 8, 1);
+    const int tile_bytes = (1 << 6) * G.pitch * (int)sizeof(int32_t);
+    const size_t smem = (size_t)tile_bytes + 8 * kStageWarpElems * sizeof(uint16_t);
+    d.tile_w = G.tile_out;
+    d.tiles = (d.p_count + G.tile_out - 1) / G.tile_out;
+    const long long items = (long long)d.tiles * d.s_count * d.a_count;
+    if (items == 0) return cudaSuccess;
+    if (items > INT32_MAX) return cudaErrorInvalidValue;
+    void (*k)(PassDesc, int, int) =
+        d.sigma > 0 ? fused_staged_kernel<1> : fused_staged_kernel<-1>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 8 * 32, smem)) !=
+        cudaSuccess)
+        return e;
+    const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(items < slots ? items : slots);
+    LaunchScope scope("forward_fused_m6_i32_final", st, pass_alg_bytes(d, 6, 2, 4));
+    k<<<grid, 8 * 32, smem, st>>>(d, (int)items, tile_bytes);
+    scope.done();
+    return cudaGetLastError();
+}
+
 template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE,
           int OP = 0>
 cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
@@ -241,6 +273,13 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     if (d.batch < 1 || d.batch > 65535) return cudaErrorInvalidValue;
     if constexpr (!kBatchable<Acc, SrcE> || OP != 0) {
         if (d.batch > 1) return cudaErrorNotSupported;
+    }
+    if constexpr (!ADJ && OP == 0 && MA == 3 && MB == 3 && std::is_same<Acc, int32_t>::value &&
+                  std::is_same<SrcE, uint16_t>::value && std::is_same<MidE, int32_t>::value &&
+                  std::is_same<DstE, int32_t>::value) {
+        if (d.hi_final && !d.lo_image && d.batch == 1 && d.n_a == 1 && staged_enabled() &&
+            !pipe_enabled())
+            return launch_staged(d, st);
     }
     if constexpr (MB > 0 && OP == 0) {
         if (pipe_enabled() && d.batch == 1) {

@@ -38,6 +38,10 @@ unsigned int read_device_counters();
 // (FHT_PIPE=1 in the environment turns it on; off by default).
 bool pipe_enabled();
 
+// Whether the final pass from a uint16 level runs as the staged persistent
+// kernel (fht_staged.cuh; FHT_STAGED=0 in the environment turns it off).
+bool staged_enabled();
+
 // Window of the level an adjoint's final pass reads (final pass of Mf levels,
 // cropped to the w_c columns p in [p_begin, p_begin + w_c), p_begin = n for
 // sign +1 and 0 for sign -1): row (s, a) is read on the w_c + 2^Mf - 1
