@@ -158,10 +158,10 @@ fht_status fhtshift(const void *in, void *out, fht_dtype dtype, int h, int w,
 
 /* fht_forward for callers that cannot allocate device memory. The paper has
  * no counterpart; this is a property of the library, not of the method.
- * Some callers cannot call cudaMalloc or anything that allocates: code that
- * runs while a CUDA graph is being captured, code confined to a memory pool
- * or budget it does not own, plugin hosts that forbid allocation after start-
- * up. This entry point computes exactly what fht_forward computes (same
+ * Some callers cannot call cudaMalloc or anything that allocates: code
+ * confined to a memory pool or budget it does not own (a framework's caching
+ * allocator, a real-time path with a fixed memory budget), plugin hosts that
+ * forbid allocation after start-up. This entry point computes exactly what fht_forward computes (same
  * arguments, minus the workspace) but keeps the intermediate butterfly levels
  * in a fixed 64 MiB device array inside the library, which every GPU that
  * loads the library holds until the process exits. It allocates nothing.

@@ -2,11 +2,9 @@
 // for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc, or any routine that allocates: code
-// that runs while a CUDA graph is being captured (allocation is not a
-// capturable operation), code running under an allocator or memory pool it
-// does not own (a framework's caching allocator, a real-time path with a
-// fixed memory budget), or a plugin host that forbids allocation after start-
-// up. fht_forward needs scratch for its intermediate butterfly levels, which
+// running under an allocator or memory pool it does not own (a framework's
+// caching allocator, a real-time path with a fixed memory budget), or a
+// plugin host that forbids allocation after start-up. fht_forward needs scratch for its intermediate butterfly levels, which
 // its caller must allocate. This entry point instead keeps that scratch in a
 // fixed device array defined in this file: the library allocates nothing at
 // call time, and every GPU that loads the library holds the array until the

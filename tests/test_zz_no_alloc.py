@@ -1,6 +1,6 @@
 """fht_forward_static: the forward transform for callers that cannot allocate
-device memory (code running during CUDA graph capture, code confined to a
-memory pool it does not own, hosts that forbid allocation after start-up).
+device memory (code confined to a memory pool or budget it does not own,
+hosts that forbid allocation after start-up).
 
 It keeps its intermediate levels in a fixed device array inside the library
 that every call shares and that keeps the last call's contents, so its output
