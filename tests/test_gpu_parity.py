@@ -393,6 +393,38 @@ def test_range_pruning_matches_full_rows(fht, h, w, q):
 
 
 
+@pytest.mark.parametrize("h,w", [(3000, 37), (37, 3000), (2049, 1001), (4096, 5)])
+def test_two_pass_4096_rows_ragged(fht, h, w):
+    """Quadrants with 4096 padded rows (two passes of six levels, the final
+    one from a uint16 level) on images of ragged sizes: fewer column tiles
+    than resident CTAs, a height that is not a power of two, single-digit
+    widths; every element of all four quadrants."""
+    img = edges_and_lines(h, w, seed=h + 3 * w)
+    x = dev(img)
+    for q in range(4):
+        got = host(fht.forward(x, q))
+        assert (got == as_i32(O.quadrant(img, q))).all(), q
+
+
+def test_two_pass_4096_rows_full_shift_range(fht):
+    """A 2500 x 2100 page (4096 padded rows and columns): full image with the
+    fused fhtshift and the [-15, 15] and [75, 105] degree ranges, every
+    element."""
+    h, w = 2500, 2100
+    img = text_stripes(h, w, seed=5)
+    x = dev(img)
+    F = O.full(img)
+    assert (host(fht.full_quadrants(x, apply_fhtshift=True)) ==
+            as_i32(O.fhtshift_full(F, h, w))).all()
+    for a, b in ((-15.0, 15.0), (75.0, 105.0)):
+        lo, hi = fht.angle_to_slopes(a, b, h, w)
+        for q in range(4):
+            if lo[q] < 0:
+                continue
+            got = host(fht.forward_range(x, q, lo[q], hi[q]))
+            assert (got == as_i32(O.range_slice(img, q, lo[q], hi[q]))).all(), (a, q)
+
+
 @pytest.mark.parametrize("h,w,q,kind", [(32768, 300, 0, "u8"), (300, 32768, 2, "u8"),
                                         (32768, 200, 1, "f32")])
 def test_max_size_32768_sampled(fht, h, w, q, kind):
