@@ -1,6 +1,8 @@
 """Tile width and kernel form of the fused passes: any FHT_TUNE setting, with
 one item per CTA (default) or the persistent pipelined kernel (FHT_PIPE=1),
-gives the same result.
+gives the same result, and so do both forms of the final pass from a uint16
+level (FHT_STAGED: the persistent staged kernel by default, or one item per
+CTA).
 
 FHT_TUNE="a,b" sets how many warp-widths of source columns one tile's first
 block of levels covers (a: first passes over uint8 images, whose shared tile
@@ -56,3 +58,34 @@ def test_tile_width_setting_is_bit_exact(tune, pipe, tmp_path):
         assert (got[f"arr_{q}"] == want).all(), (tune, q)
     for i, q in enumerate((0, 2)):
         assert (got[f"arr_{4 + i}"] == O.quadrant(f, q, kind="f32")).all(), (tune, q)
+
+
+CHILD_4096 = r"""
+import sys
+import numpy as np
+import torch
+import paper_1811_06378_gb300 as fht
+from workloads import edges_and_lines
+out = [fht.forward(torch.from_numpy(edges_and_lines(h, w, seed=h + w)).cuda(), q).cpu().numpy()
+       for h, w, q in ((2500, 300, 0), (2500, 300, 1), (300, 2500, 2), (300, 2500, 3))]
+np.savez(sys.argv[1], *out)
+"""
+
+
+@pytest.mark.parametrize("staged", ["0", "1"])
+def test_final_pass_from_uint16_level_both_forms(staged, tmp_path):
+    """The final pass of a 4096-row quadrant of a uint8 image runs as the
+    persistent staged kernel (default) or, with FHT_STAGED=0, as the
+    one-item-per-CTA kernel; both give the oracle's result bit for bit."""
+    import oracle as O
+    from workloads import edges_and_lines
+    path = str(tmp_path / "out.npz")
+    env = dict(os.environ, FHT_STAGED=staged, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", CHILD_4096, path], env=env, cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = np.load(path)
+    for i, (h, w, q) in enumerate(((2500, 300, 0), (2500, 300, 1), (300, 2500, 2),
+                                   (300, 2500, 3))):
+        want = O.quadrant(edges_and_lines(h, w, seed=h + w), q)
+        assert (got[f"arr_{i}"] == want.astype(np.int64).astype(np.int32)).all(), (staged, q)
