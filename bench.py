@@ -14,9 +14,10 @@ map (5% Bernoulli edge pixels + 4 rasterised lines, seed 4096 + rank):
 value = input megapixels per second over the whole step (all ranks).
 Timing: CUDA events on the stream the kernels run on, L2 flushed (a 512 MiB
 write) before every timed step, W >= 3 warm-up steps. The timed region
-replays the step captured as one CUDA graph; the per-kernel launch times
-behind the roofline come from a second region of the same K steps launched
-call by call with the library's per-launch CUDA events. Per-row times, the
+replays the step captured as one CUDA graph (the four quadrants of the
+full-layout calls on four streams); the per-kernel launch times behind the
+roofline come from a second region of the same K steps launched call by call,
+every launch timed alone with the library's per-launch CUDA events. Per-row times, the
 plain single-quadrant forward (the headline FHT at 4096^2 int32) and the
 batched path are reported under "rows".
 
@@ -322,28 +323,37 @@ def run_ours(args):
     gen = torch.Generator(device=dev).manual_seed(7 + rank)
     grad = torch.randn((R, Wf), generator=gen, device=dev, dtype=torch.float32)
     gimg = torch.empty((S, S), dtype=torch.float32, device=dev)
-    ws_bytes = max(fht.workspace_size(S, S, fht.LAYOUT_FULL, 0, torch.uint8, torch.int32),
-                   fht.workspace_size(S, S, fht.LAYOUT_FULL, 0, torch.float32, torch.float32),
-                   fht.workspace_size(S, S, fht.LAYOUT_QUADRANT, 0, torch.uint8, torch.int32),
-                   fht.workspace_size(S, S, fht.LAYOUT_QUADRANT, 1, torch.uint8, torch.int32))
-    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    # one workspace per row (the full-layout ones hold a slice per quadrant)
+    ws_full = torch.empty(max(fht.workspace_size(S, S, fht.LAYOUT_FULL, 0, torch.uint8,
+                                                 torch.int32), 1),
+                          dtype=torch.uint8, device=dev)
+    ws_rng = torch.empty(max(fht.workspace_size(S, S, fht.LAYOUT_QUADRANT, q, torch.uint8,
+                                                torch.int32) for q in (0, 1)),
+                         dtype=torch.uint8, device=dev)
+    ws_adj = torch.empty(max(fht.workspace_size(S, S, fht.LAYOUT_FULL, 0, torch.float32,
+                                                torch.float32), 1),
+                         dtype=torch.uint8, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     H0 = torch.empty((n0, W0), dtype=torch.int32, device=dev)
 
     def row_full():
-        fht.full_quadrants(img, out=F, workspace=ws)
+        fht.full_quadrants(img, out=F, workspace=ws_full)
 
     def row_shift():
         fht.fhtshift(F, S, S, fht.LAYOUT_FULL, out=Fs)
 
     def row_range():
         for q in used:
-            fht.forward_range(img, q, lo[q], hi[q], out=rng_out[q], workspace=ws)
+            fht.forward_range(img, q, lo[q], hi[q], out=rng_out[q], workspace=ws_rng)
 
     def row_adjoint():
-        fht.adjoint(grad, S, S, fht.LAYOUT_FULL, out=gimg, workspace=ws)
+        fht.adjoint(grad, S, S, fht.LAYOUT_FULL, out=gimg, workspace=ws_adj)
 
     def step():
+        # the rows one after another on one stream (the full-layout calls run
+        # their four quadrants concurrently inside the library). Running the
+        # rows themselves on three streams as well was measured slower (1.053
+        # against 1.030 ms per step): the quadrants already fill the GPU.
         row_full()
         row_shift()
         row_range()
@@ -440,9 +450,11 @@ def run_ours(args):
                                "4-quadrant image, fhtshift, [-15,15] deg range, FP32 "
                                "full adjoint", "l2": "flushed before every timed step",
                    "parallelism": f"replicas x{world}",
-                   "timing": "value: K replays of the step captured as one CUDA graph; "
+                   "timing": "value: K replays of the step captured as one CUDA graph "
+                             "(the quadrants of the full-layout calls on four streams); "
                              "roofline and kernels: a second region of the same K steps "
-                             "launched call by call with per-launch CUDA events",
+                             "launched call by call, every launch timed alone with "
+                             "per-launch CUDA events",
                    "profiled_ms_per_step": prof_total_ms / args.steps,
                    "host_cores": (f"{len(near_cpus)} cores local to the GPU" if near_cpus
                                   else "unbound"),
@@ -493,16 +505,16 @@ def run_ours(args):
             if out_free[i % 2] is not None:
                 s_cmp.wait_event(out_free[i % 2])
             s_cmp.wait_event(e_img)
-            fht.full_quadrants(b["img"], out=b["F"], workspace=ws, stream=s_cmp)
+            fht.full_quadrants(b["img"], out=b["F"], workspace=ws_full, stream=s_cmp)
             e_f = ev(); e_f.record(s_cmp)
             fht.fhtshift(b["F"], S, S, fht.LAYOUT_FULL, out=b["Fs"], stream=s_cmp)
             e_fs = ev(); e_fs.record(s_cmp)
             for q in used:
-                fht.forward_range(b["img"], q, lo[q], hi[q], out=b[f"r{q}"], workspace=ws,
+                fht.forward_range(b["img"], q, lo[q], hi[q], out=b[f"r{q}"], workspace=ws_rng,
                                   stream=s_cmp)
             e_r = ev(); e_r.record(s_cmp)
             s_cmp.wait_event(e_grad)
-            fht.adjoint(b["grad"], S, S, fht.LAYOUT_FULL, out=b["g"], workspace=ws,
+            fht.adjoint(b["grad"], S, S, fht.LAYOUT_FULL, out=b["g"], workspace=ws_adj,
                         stream=s_cmp)
             e_g = ev(); e_g.record(s_cmp)
             in_free[i % 2] = e_g
@@ -551,7 +563,7 @@ def run_ours(args):
                     "frac_of_measured_hbm": alg_bytes / (t / 1e3) / 1e9 / peak,
                     "frac_of_8tbs": alg_bytes / (t / 1e3) / 1e9 / NOMINAL_HBM_GBS}
         rows["forward_q0_int32"] = row_entry(
-            lambda: fht.forward(img, 0, out=H0, workspace=ws), S * S + n0 * W0 * 4, S * S)
+            lambda: fht.forward(img, 0, out=H0, workspace=ws_rng), S * S + n0 * W0 * 4, S * S)
         rows["full_quadrants_int32"] = row_entry(row_full, S * S + R * Wf * 4, S * S)
         rows["fhtshift_full_int32"] = row_entry(row_shift, 2 * R * Wf * 4, S * S)
         rows["range_pm15deg_int32"] = row_entry(
@@ -610,7 +622,7 @@ def run_ours(args):
         del sh_out, sh_ws
         # other operations: the maximum along every pattern of Q0
         rows["max_q0_int32"] = row_entry(
-            lambda: fht.forward_op(img, 0, fht.OP_MAX, out=H0, workspace=ws),
+            lambda: fht.forward_op(img, 0, fht.OP_MAX, out=H0, workspace=ws_adj),
             S * S + n0 * W0 * 4, S * S)
         # back to lines: the strongest line of every slope of the full image
         rows["row_argmax_full_int32"] = row_entry(lambda: fht.row_argmax(F), R * Wf * 4, S * S)

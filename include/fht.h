@@ -108,7 +108,12 @@ fht_status fht_angle_to_slopes(double phi_lo_deg, double phi_hi_deg, int h, int 
 
 /* Bytes of device workspace needed by fht_forward, fht_forward_range,
  * fht_full_quadrants and fht_adjoint on an h x w image with this layout,
- * quadrant (ignored for FHT_LAYOUT_FULL) and type pair. May be 0. */
+ * quadrant (ignored for FHT_LAYOUT_FULL) and type pair. May be 0.
+ * For FHT_LAYOUT_FULL it is one slice per quadrant, which lets the four
+ * quadrants run concurrently (the library's default schedule;
+ * FHT_CONCURRENT=0 in the environment when the library loads turns it off);
+ * any workspace down to the largest single quadrant's is accepted and runs
+ * the quadrants one after another. */
 fht_status fht_workspace_size(int h, int w, fht_layout layout, fht_quadrant q,
                               fht_dtype in_t, fht_dtype acc_t, size_t *bytes);
 
@@ -137,7 +142,14 @@ fht_status fht_forward_range(const void *img, fht_dtype in_t, int h, int w,
  * straight into the concatenated layout (Q0 flipped, Q1, Q2 flipped, Q3; one
  * copy of each shared seam row). out is fht_full_shape rows x cols.
  * apply_fhtshift != 0 additionally rotates every row as fhtshift does
- * (Section 5), fused into the same stores. */
+ * (Section 5), fused into the same stores.
+ * With a workspace of fht_workspace_size bytes and the concurrent schedule on,
+ * the quadrants run on the caller's stream and three streams of the library,
+ * forked from and joined back into `stream` with events (stream capture turns
+ * them into graph branches); work enqueued on `stream` afterwards still sees
+ * the whole result. The library's streams are shared by every call on a
+ * device: do not run such a call on one host thread while another thread is
+ * capturing one. */
 fht_status fht_full_quadrants(const void *img, fht_dtype in_t, int h, int w,
                               int64_t in_pitch, void *out, fht_dtype acc_t,
                               int64_t out_pitch, int apply_fhtshift, void *workspace,
@@ -188,7 +200,9 @@ fht_status fht_forward_static(const void *img, fht_dtype in_t, int h, int w,
  * reverse (each merge becomes a split). grad_hough has the forward output's
  * shape, type dtype (FHT_F32 or FHT_I32), pitch in_pitch; grad_img is h x w
  * of the same type, pitch out_pitch, fully overwritten. For the full layout the
- * four quadrant contributions are summed in the order Q0, Q1, Q2, Q3. */
+ * four quadrant contributions are summed in the order Q0, Q1, Q2, Q3 (also
+ * under the concurrent schedule of fht_full_quadrants, where the passes before
+ * each quadrant's final one overlap and the final passes stay in order). */
 fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
                        fht_layout layout, fht_quadrant q, int64_t in_pitch,
                        void *grad_img, int64_t out_pitch, void *workspace,

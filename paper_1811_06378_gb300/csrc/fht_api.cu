@@ -254,6 +254,7 @@ struct Tune {
     int n_a_wide = 1;   // 4-byte shared tiles
     bool pipe = false;
     bool staged = true;
+    bool concurrent = true;
     Tune() {
         if (const char *e = getenv("FHT_TUNE")) {
             int a = 0, b = 0;
@@ -264,6 +265,7 @@ struct Tune {
         }
         if (const char *e = getenv("FHT_PIPE")) pipe = e[0] == '1' && e[1] == 0;
         if (const char *e = getenv("FHT_STAGED")) staged = !(e[0] == '0' && e[1] == 0);
+        if (const char *e = getenv("FHT_CONCURRENT")) concurrent = !(e[0] == '0' && e[1] == 0);
     }
 };
 const Tune g_tune;
@@ -385,8 +387,17 @@ fht_status run_forward(const QuadPlan &P, const Side &image, const Side &out,
 // (transposed) image and written, or added, into grad_img.
 fht_status run_adjoint(const QuadPlan &P, const Side &grad_img, const Side &grad_hough,
                        const FinalMap &fm, int acc_elem, int accumulate, void *ws,
-                       cudaStream_t st, const Batch &B = Batch{}) {
+                       cudaStream_t st, const Batch &B = Batch{},
+                       cudaEvent_t before_final = nullptr) {
     for (int p = 0; p < P.npass; ++p) {
+        if (before_final && p == P.npass - 1) {
+            // the final pass adds into an image gradient another stream writes
+            const cudaError_t e = cudaStreamWaitEvent(st, before_final, 0);
+            if (e != cudaSuccess) {
+                g_last_cuda_error = (int)e;
+                return FHT_ECUDA;
+            }
+        }
         // output rows y < h_c of the opposite-sign transform are the image rows
         PassDesc d = pass_desc(P, p, grad_hough, grad_img, ws, FinalMap{0, P.n - 1, 0, 1, 0, 0},
                                0, P.h_c - 1, B);
@@ -432,6 +443,107 @@ fht_status run_adjoint(const QuadPlan &P, const Side &grad_img, const Side &grad
 
 bool sizes_ok(int h, int w) { return h >= 1 && w >= 1 && h <= kMaxSide && w <= kMaxSide; }
 bool quadrant_ok(int q) { return q >= 0 && q <= 3; }
+
+// ------------------------------------------------------------ concurrent quadrants
+// The four quadrants of a full transform are independent: the forward writes
+// disjoint rows of the full image, and the adjoint's passes before the final
+// one read disjoint rows of the gradient. Given a workspace slice each, they
+// run on four streams -- the caller's and three of the library's, forked from
+// and joined back into the caller's stream with events, which stream capture
+// turns into graph branches -- so one quadrant's launch tails overlap
+// another's work. The adjoint's final passes all add into the one image
+// gradient, so they stay in quadrant order (an event chain). Each device has
+// kForkSets sets of streams, taken by successive calls in turn, so that calls
+// the caller runs concurrently on its own streams do not queue behind each
+// other on the library's; a mutex keeps each call's fork-join sequence whole.
+// The streams and events are created by the first call on a device that is
+// not being captured; a call captured before then runs its quadrants one
+// after another. While per-launch profiling is on, quadrants also run one
+// after another so that every launch is timed alone.
+constexpr int kForkDevices = 64;
+constexpr int kForkSets = 4;
+struct ForkState {
+    cudaStream_t lane[3] = {};
+    cudaEvent_t fork = nullptr, join[3] = {}, chain[4] = {};
+};
+std::mutex g_fork_mu;
+ForkState g_fork[kForkDevices][kForkSets];
+bool g_fork_ready[kForkDevices] = {};
+unsigned g_fork_next[kForkDevices] = {};
+
+bool profiling_on() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    return g_prof_on;
+}
+
+bool use_concurrent(size_t ws_bytes, size_t concurrent_bytes) {
+    return g_tune.concurrent && concurrent_bytes > 0 && ws_bytes >= concurrent_bytes &&
+           !profiling_on();
+}
+
+class QuadFork {
+  public:
+    explicit QuadFork(cudaStream_t st) : st_(st), lk_(g_fork_mu) {}
+    // Sets up this device's streams and events on first use, then makes the
+    // library's streams wait for the work already on the caller's stream.
+    // FHT_EUNSUPPORTED (nothing enqueued): the streams do not exist yet and
+    // the caller's stream is being captured; run the quadrants serially.
+    fht_status begin() {
+        int dev = -1;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess || dev < 0 || dev >= kForkDevices) return fail(e);
+        if (!g_fork_ready[dev]) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if ((e = cudaStreamIsCapturing(st_, &cs)) != cudaSuccess) return fail(e);
+            if (cs != cudaStreamCaptureStatusNone) return FHT_EUNSUPPORTED;
+            const unsigned fl = cudaEventDisableTiming;
+            for (int k = 0; k < kForkSets && e == cudaSuccess; ++k) {
+                ForkState &S = g_fork[dev][k];
+                for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+                    e = cudaStreamCreateWithFlags(&S.lane[i], cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.fork, fl);
+                for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+                    e = cudaEventCreateWithFlags(&S.join[i], fl);
+                for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+                    e = cudaEventCreateWithFlags(&S.chain[i], fl);
+            }
+            if (e != cudaSuccess) return fail(e);
+            g_fork_ready[dev] = true;
+        }
+        F_ = &g_fork[dev][g_fork_next[dev]++ % kForkSets];
+        if ((e = cudaEventRecord(F_->fork, st_)) != cudaSuccess) return fail(e);
+        for (int i = 0; i < 3; ++i) {
+            if ((e = cudaStreamWaitEvent(F_->lane[i], F_->fork, 0)) != cudaSuccess) return fail(e);
+            forked_ = i + 1;
+        }
+        return FHT_OK;
+    }
+    cudaStream_t stream(int q) const { return q == 0 ? st_ : F_->lane[q - 1]; }
+    cudaEvent_t chain(int q) const { return F_->chain[q]; }
+    // Joins every forked stream back into the caller's stream (also after a
+    // failed launch: a capture must not end with a stream left out).
+    fht_status end() {
+        fht_status s = FHT_OK;
+        for (int i = 0; i < forked_; ++i) {
+            cudaError_t e = cudaEventRecord(F_->join[i], F_->lane[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st_, F_->join[i], 0);
+            if (e != cudaSuccess) s = fail(e);
+        }
+        forked_ = 0;
+        return s;
+    }
+    ~QuadFork() { end(); }
+
+  private:
+    static fht_status fail(cudaError_t e) {
+        g_last_cuda_error = (int)(e != cudaSuccess ? e : cudaErrorInvalidDevice);
+        return FHT_ECUDA;
+    }
+    cudaStream_t st_;
+    std::lock_guard<std::mutex> lk_;
+    ForkState *F_ = nullptr;
+    int forked_ = 0;
+};
 
 // fhtshift as a standalone permutation: one block row per Hough row.
 struct ShiftRows {
@@ -598,10 +710,11 @@ fht_status fht_workspace_size(int h, int w, fht_layout layout, fht_quadrant q,
     // the adjoint of an (acc, acc) transform runs full-width intermediates
     const bool adj = in_t == acc_t;
     if (layout == FHT_LAYOUT_FULL) {
+        // one slice per quadrant, so that the quadrants can run concurrently
         for (int qq = 0; qq < 4; ++qq) {
-            need = std::max(need, plan_workspace(make_plan(h, w, qq, true, elem_of(in_t), acc)));
-            if (adj)
-                need = std::max(need, plan_workspace(make_plan(h, w, qq, true, acc, acc, true)));
+            size_t one = plan_workspace(make_plan(h, w, qq, true, elem_of(in_t), acc));
+            if (adj) one = std::max(one, plan_workspace(make_plan(h, w, qq, true, acc, acc, true)));
+            need += one;
         }
     } else if (layout == FHT_LAYOUT_QUADRANT) {
         if (!quadrant_ok(q)) return FHT_EINVAL;
@@ -660,21 +773,37 @@ fht_status fht_full_quadrants(const void *img, fht_dtype in_t, int h, int w,
     int hp = next_pow2(h), wp = next_pow2(w);
     if (ilog2(hp) > kMaxK || ilog2(wp) > kMaxK) return FHT_EINVAL;
     if (out_pitch < hp + wp) return FHT_EINVAL;
-    size_t need = 0;
+    size_t need = 0, sum = 0;
     QuadPlan plans[4];
     for (int q = 0; q < 4; ++q) {
         plans[q] = make_plan(h, w, q, true, elem_of(in_t), acc);
         need = std::max(need, plan_workspace(plans[q]));
+        sum += plan_workspace(plans[q]);
     }
     if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
-    for (int q = 0; q < 4; ++q) {
+    auto run_q = [&](int q, void *ws, cudaStream_t st) {
         const QuadPlan &P = plans[q];
         Side image{const_cast<void *>(img), in_pitch, elem_of(in_t), P.h_c, P.w_c};
         Side o{out, out_pitch, elem_of(acc_t), 0, P.W};
         FinalMap fm = full_map(q, hp, wp);
         fm.shift_on = apply_fhtshift ? 1 : 0;
-        fht_status s = run_forward(P, image, o, fm, fm.t_first, fm.t_last, acc, workspace,
-                                   (cudaStream_t)stream);
+        return run_forward(P, image, o, fm, fm.t_first, fm.t_last, acc, ws, st);
+    };
+    if (use_concurrent(workspace_bytes, sum)) {
+        QuadFork f((cudaStream_t)stream);
+        fht_status s = f.begin();
+        if (s != FHT_EUNSUPPORTED) {
+            char *ws = static_cast<char *>(workspace);
+            for (int q = 0; q < 4 && s == FHT_OK; ++q) {
+                s = run_q(q, ws, f.stream(q));
+                ws += plan_workspace(plans[q]);
+            }
+            const fht_status j = f.end();
+            return s != FHT_OK ? s : j;
+        }
+    }
+    for (int q = 0; q < 4; ++q) {
+        fht_status s = run_q(q, workspace, (cudaStream_t)stream);
         if (s != FHT_OK) return s;
     }
     return FHT_OK;
@@ -750,18 +879,43 @@ fht_status fht_adjoint(const void *grad_hough, fht_dtype dtype, int h, int w,
     int hp = next_pow2(h), wp = next_pow2(w);
     if (ilog2(hp) > kMaxK || ilog2(wp) > kMaxK || in_pitch < hp + wp) return FHT_EINVAL;
     QuadPlan plans[4];
-    size_t need = 0;
+    size_t need = 0, sum = 0;
     for (int qq = 0; qq < 4; ++qq) {
         plans[qq] = make_plan(h, w, qq, true, acc, acc, true);
         need = std::max(need, plan_workspace(plans[qq]));
+        sum += plan_workspace(plans[qq]);
     }
     if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
-    for (int qq = 0; qq < 4; ++qq) {
+    auto run_q = [&](int qq, void *ws, cudaStream_t s_q, cudaEvent_t before_final) {
         const QuadPlan &P = plans[qq];
         Side gi{grad_img, out_pitch, acc, P.h_c, P.w_c};
         Side gh{const_cast<void *>(grad_hough), in_pitch, acc, 0, P.W};
-        fht_status s = run_adjoint(P, gi, gh, full_map(qq, hp, wp), acc, qq > 0 ? 1 : 0,
-                                   workspace, st);
+        return run_adjoint(P, gi, gh, full_map(qq, hp, wp), acc, qq > 0 ? 1 : 0, ws, s_q,
+                           Batch{}, before_final);
+    };
+    if (use_concurrent(workspace_bytes, sum)) {
+        // quadrant qq's final pass waits for quadrant qq-1's (event chain)
+        QuadFork f(st);
+        fht_status s = f.begin();
+        if (s != FHT_EUNSUPPORTED) {
+            char *ws = static_cast<char *>(workspace);
+            for (int qq = 0; qq < 4 && s == FHT_OK; ++qq) {
+                s = run_q(qq, ws, f.stream(qq), qq > 0 ? f.chain(qq - 1) : nullptr);
+                if (s == FHT_OK) {
+                    const cudaError_t e = cudaEventRecord(f.chain(qq), f.stream(qq));
+                    if (e != cudaSuccess) {
+                        g_last_cuda_error = (int)e;
+                        s = FHT_ECUDA;
+                    }
+                }
+                ws += plan_workspace(plans[qq]);
+            }
+            const fht_status j = f.end();
+            return s != FHT_OK ? s : j;
+        }
+    }
+    for (int qq = 0; qq < 4; ++qq) {
+        fht_status s = run_q(qq, workspace, st, nullptr);
         if (s != FHT_OK) return s;
     }
     return FHT_OK;
