@@ -180,7 +180,7 @@ fht_status fhtshift(const void *in, void *out, fht_dtype dtype, int h, int w,
  *
  * Limit: requests for which fht_workspace_size(h, w, FHT_LAYOUT_QUADRANT, q,
  * in_t, acc_t) exceeds 64 MiB return FHT_ENOMEM and enqueue nothing (a uint8
- * image up to 4096 x 4096 into int32 fits).
+ * image up to 4096 x 4096 into int32 fits, with the default tuning).
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.
@@ -411,6 +411,34 @@ void fht_plan_destroy(fht_plan *plan);
  * and its output is incomplete) and resets the count, else FHT_OK; FHT_ECUDA
  * if the device could not be synchronised. Not in the paper. */
 fht_status fht_device_status(void);
+
+/* ------------------------------------------------------------ tuning
+ * How the plain sum transforms and adjoints (fht_forward, fht_forward_range,
+ * fht_full_quadrants, fht_adjoint, the uniform batches, fht_forward_static)
+ * of quadrants with n = 2^K rows are split into fused passes and tiled. Not
+ * in the paper (it fixes what is computed, not how the work is cut); every
+ * setting gives the same results bit for bit. The package's autotuner times
+ * the candidates on the GPU and sets the fastest per K. */
+typedef struct {
+    int max_levels;   /* most butterfly levels one pass fuses ("stages per
+                         CTA"): 4, 5 or 6; the K levels are split into
+                         ceil(K / max_levels) passes as evenly as possible */
+    int tile_u8;      /* warp-widths (248 columns each) of source columns per
+                         tile in first passes over uint8 images: 1, 2 or 3 */
+    int tile_wide;    /* the same for passes with 4-byte shared tiles: 1..3 */
+} fht_tuning;
+
+/* Use `t` for quadrants with 2^K rows (1 <= K <= 15) in calls made from now
+ * on, process-wide (a CUDA graph keeps the plan it captured). Workspace sizes
+ * follow the tuning: query fht_workspace_size after setting it (a call whose
+ * workspace is too small for its plan returns FHT_EINVAL). t == NULL restores
+ * the default (6 levels; tile widths 1, or those of FHT_TUNE="a,b" in the
+ * environment when the library loads). FHT_EINVAL for K or values out of
+ * range. */
+fht_status fht_set_tuning(int K, const fht_tuning *t);
+
+/* The tuning in use for quadrants with 2^K rows (HOST struct). */
+fht_status fht_get_tuning(int K, fht_tuning *out);
 
 /* ------------------------------------------------------------ profiling
  * Kernel-level timing for benchmarks; normal use never needs it. Not in the

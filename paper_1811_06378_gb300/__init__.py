@@ -15,6 +15,7 @@ variant (Section 4) and fhtshift (Section 5), plus the adjoint.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -41,6 +42,12 @@ _DTYPE = {torch.uint8: _U8, torch.int32: _I32, torch.float32: _F32}
 
 class FHTError(RuntimeError):
     """A libfht call returned a status other than FHT_OK."""
+
+
+class Tuning(ctypes.Structure):
+    """fht_tuning: levels fused per pass and tile widths for 2^K-row quadrants."""
+    _fields_ = [("max_levels", ctypes.c_int), ("tile_u8", ctypes.c_int),
+                ("tile_wide", ctypes.c_int)]
 
 
 def _load() -> ctypes.CDLL:
@@ -86,6 +93,8 @@ def _load() -> ctypes.CDLL:
         "fht_forward_many": (i, [vp, i, i64, i, i, i64, i, i, vp, i64, i64, vp, sz, vp]),
         "fht_adjoint_many": (i, [vp, i, i64, i, i, i, i, i64, vp, i64, i64, vp, sz, vp]),
     }
+    sigs["fht_set_tuning"] = (i, [i, ctypes.POINTER(Tuning)])
+    sigs["fht_get_tuning"] = (i, [i, ctypes.POINTER(Tuning)])
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
         fn.restype = res
@@ -121,6 +130,50 @@ def _dev2d(t: torch.Tensor, name: str) -> tuple[int, int]:
     if t.dtype not in _DTYPE:
         raise ValueError(f"{name}: unsupported dtype {t.dtype}")
     return _DTYPE[t.dtype], max(t.stride(0), t.shape[1])
+
+
+# ------------------------------------------------------------------ tuning
+
+def set_tuning(K: int, max_levels: int | None = None, tile_u8: int = 1,
+               tile_wide: int = 1) -> None:
+    """Tuning for quadrants with 2^K rows from now on (fht_set_tuning);
+    max_levels=None restores the default."""
+    if max_levels is None:
+        _check(lib.fht_set_tuning(K, None), "fht_set_tuning")
+        return
+    t = Tuning(max_levels, tile_u8, tile_wide)
+    _check(lib.fht_set_tuning(K, ctypes.byref(t)), "fht_set_tuning")
+
+
+def get_tuning(K: int) -> tuple[int, int, int]:
+    """(max_levels, tile_u8, tile_wide) in use for 2^K-row quadrants."""
+    t = Tuning()
+    _check(lib.fht_get_tuning(K, ctypes.byref(t)), "fht_get_tuning")
+    return t.max_levels, t.tile_u8, t.tile_wide
+
+
+TUNING_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
+
+
+def load_tuning(path: str) -> dict:
+    """Apply an autotuner table (JSON, see autotune.py) to the library."""
+    with open(path) as f:
+        res = json.load(f)
+    for k, e in res["table"].items():
+        set_tuning(int(k), int(e["max_levels"]), int(e["tile_u8"]), int(e["tile_wide"]))
+    return res
+
+
+def _load_default_tuning() -> None:
+    """The autotuner's table for this GPU (tuning_gb300.json), or the file
+    FHT_TUNE_FILE names; FHT_TUNE_FILE=none keeps the library's defaults."""
+    path = os.environ.get("FHT_TUNE_FILE")
+    if path is None:
+        path = TUNING_FILE if os.path.exists(TUNING_FILE) else None
+    elif path.lower() == "none":
+        path = None
+    if path:
+        load_tuning(path)
 
 
 # ------------------------------------------------------------------ geometry
@@ -608,3 +661,6 @@ class FHTFunction(torch.autograd.Function):
         if g.dim() == 2:
             return adjoint(g, ctx.h, ctx.w, ctx.layout, ctx.q), None, None
         return adjoint_many(g, ctx.h, ctx.w, ctx.layout, ctx.q), None, None
+
+
+_load_default_tuning()

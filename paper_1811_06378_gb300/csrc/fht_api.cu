@@ -101,12 +101,22 @@ size_t elem_bytes(int e) { return e == kU8 ? 1 : e == kU16 ? 2 : 4; }
 
 // Split K levels into passes of at most kMaxLevelsPerPass, as even as possible,
 // larger passes first.
-int split_levels(int K, int *m) {
+int split_levels(int K, int *m, int max_levels = kMaxLevelsPerPass) {
     if (K == 0) { m[0] = 0; return 1; }
-    int P = (K + kMaxLevelsPerPass - 1) / kMaxLevelsPerPass;
+    int P = (K + max_levels - 1) / max_levels;
     for (int p = 0; p < P; ++p) m[p] = K / P + (p < K % P ? 1 : 0);
     return P;
 }
+
+// Tuning of the plain sum transforms and adjoints with 2^K rows: the most
+// levels one pass fuses (stages per CTA) and the tile widths in warp-widths of
+// source columns (first passes over uint8 images; passes with 4-byte shared
+// tiles). Set by fht_set_tuning (an autotuner's results); defaults 6 levels
+// and the FHT_TUNE widths.
+struct TuneK {
+    int max_levels, tile_u16, tile_wide;
+};
+TuneK tuning_for(int K);
 
 // Geometry and pass plan of one quadrant transform.
 struct QuadPlan {
@@ -118,6 +128,7 @@ struct QuadPlan {
     int n, K, W;
     int w_in;           // meaningful width used by fhtshift
     int npass;
+    bool tuned;         // a plain sum transform or adjoint: the tuning table applies
     int m[4], k[5];
     int lvl_type[5];    // element type of intermediate level k[p] (1 <= p < npass)
     int lvl_cols[5];
@@ -156,7 +167,8 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
         P.W = P.w_c + P.n;
         P.w_in = P.w_c;
     }
-    P.npass = split_levels(P.K, P.m);
+    P.tuned = op == 0 && !sheared;
+    P.npass = split_levels(P.K, P.m, P.tuned ? tuning_for(P.K).max_levels : kMaxLevelsPerPass);
     P.k[0] = 0;
     for (int p = 0; p < P.npass; ++p) P.k[p + 1] = P.k[p] + P.m[p];
     P.buf_bytes[0] = P.buf_bytes[1] = 0;
@@ -166,8 +178,10 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
     for (int p = 1; p < P.npass; ++p) {
         int k = P.k[p];
         int type = acc_elem;
-        // u8 images summed over 2^k rows stay below 2^16 while k <= 8
-        if (acc_elem == kI32 && in_elem == kU8 && k <= 8 && !adjoint) type = kU16;
+        // u8 images summed over 2^k rows stay below 2^16 while k <= 8 (the
+        // sum's passes from a uint16 level write int32: only the first level)
+        if (acc_elem == kI32 && in_elem == kU8 && k <= 8 && !adjoint && (p == 1 || op != 0))
+            type = kU16;
         // the maximum or minimum of uint8 values is one of them: uint16 at every level
         if (acc_elem == kI32 && in_elem == kU8 && op != 0) type = kU16;
         P.lvl_type[p] = type;
@@ -270,6 +284,19 @@ struct Tune {
 };
 const Tune g_tune;
 
+// The tuning table (index K = 1..15), guarded by g_tune_mu; entries never set
+// hold the defaults.
+constexpr int kTuneSlots = 16;
+std::mutex g_tune_mu;
+TuneK g_tune_k[kTuneSlots];
+bool g_tune_set[kTuneSlots] = {};
+
+TuneK tuning_for(int K) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (K >= 0 && K < kTuneSlots && g_tune_set[K]) return g_tune_k[K];
+    return TuneK{kMaxLevelsPerPass, g_tune.n_a_u16, g_tune.n_a_wide};
+}
+
 std::mutex &counter_mu() {
     static std::mutex mu;
     return mu;
@@ -360,7 +387,9 @@ PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &fina
     // block A has 2^MB items per warp-column: widen it until every warp has one
     if (P.m[p] >= 4) {
         const int rb = 1 << (P.m[p] - 3);
-        const int base = acc_is_u16_mid(P, p) ? g_tune.n_a_u16 : g_tune.n_a_wide;
+        const TuneK t = P.tuned ? tuning_for(P.K) : TuneK{kMaxLevelsPerPass, g_tune.n_a_u16,
+                                                            g_tune.n_a_wide};
+        const int base = acc_is_u16_mid(P, p) ? t.tile_u16 : t.tile_wide;
         d.n_a = std::max(base, 8 / rb);
     } else {
         d.n_a = 1;
@@ -1168,6 +1197,26 @@ fht_status fht_adjoint_many(const void *grad_hough, int batch, int64_t grad_batc
         s = run_adjoint(P, gi, gh, full_map(qq, hp, wp), kF32, qq > 0 ? 1 : 0, workspace, st, B);
         if (s != FHT_OK) return s;
     }
+    return FHT_OK;
+}
+
+fht_status fht_set_tuning(int K, const fht_tuning *t) {
+    if (K < 1 || K > kMaxK) return FHT_EINVAL;
+    if (t && (t->max_levels < 4 || t->max_levels > kMaxLevelsPerPass || t->tile_u8 < 1 ||
+              t->tile_u8 > 3 || t->tile_wide < 1 || t->tile_wide > 3))
+        return FHT_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (t) g_tune_k[K] = TuneK{t->max_levels, t->tile_u8, t->tile_wide};
+    g_tune_set[K] = t != nullptr;
+    return FHT_OK;
+}
+
+fht_status fht_get_tuning(int K, fht_tuning *out) {
+    if (K < 1 || K > kMaxK || !out) return FHT_EINVAL;
+    const TuneK t = tuning_for(K);
+    out->max_levels = t.max_levels;
+    out->tile_u8 = t.tile_u16;
+    out->tile_wide = t.tile_wide;
     return FHT_OK;
 }
 

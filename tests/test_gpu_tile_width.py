@@ -46,7 +46,7 @@ def test_tile_width_setting_is_bit_exact(tune, pipe, tmp_path):
     import oracle as O
     from workloads import edges_and_lines, random_image
     path = str(tmp_path / "out.npz")
-    env = dict(os.environ, FHT_TUNE=tune, FHT_PIPE=pipe, PYTHONPATH=ROOT)
+    env = dict(os.environ, FHT_TUNE=tune, FHT_PIPE=pipe, FHT_TUNE_FILE="none", PYTHONPATH=ROOT)
     r = subprocess.run([sys.executable, "-c", CHILD, path], env=env, cwd=ROOT,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -80,7 +80,7 @@ def test_final_pass_from_uint16_level_both_forms(staged, tmp_path):
     import oracle as O
     from workloads import edges_and_lines
     path = str(tmp_path / "out.npz")
-    env = dict(os.environ, FHT_STAGED=staged, PYTHONPATH=ROOT)
+    env = dict(os.environ, FHT_STAGED=staged, FHT_TUNE_FILE="none", PYTHONPATH=ROOT)
     r = subprocess.run([sys.executable, "-c", CHILD_4096, path], env=env, cwd=ROOT,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]

@@ -1,0 +1,84 @@
+"""The tuning entry points without a GPU: argument checks, set / get /
+restore, workspace sizes that follow the pass split, and an autotuner table
+applied through the binding."""
+
+import json
+
+import pytest
+import torch
+
+
+@pytest.fixture(scope="module")
+def fht():
+    import __graft_entry__
+    __graft_entry__._builder().build()
+    import paper_1811_06378_gb300 as m
+    return m
+
+
+@pytest.fixture
+def restore(fht):
+    saved = {K: fht.get_tuning(K) for K in range(1, 16)}
+    yield
+    for K, t in saved.items():
+        fht.set_tuning(K, *t)
+
+
+def test_bad_tunings_rejected(fht, restore):
+    for K, t in [(0, (6, 1, 1)), (16, (6, 1, 1)), (12, (3, 1, 1)), (12, (7, 1, 1)),
+                 (12, (6, 0, 1)), (12, (6, 1, 4))]:
+        with pytest.raises(fht.FHTError):
+            fht.set_tuning(K, *t)
+    assert fht.lib.fht_get_tuning(12, None) == 1
+
+
+def test_set_get_and_default(fht, restore):
+    fht.set_tuning(12, None)
+    default = fht.get_tuning(12)
+    assert default[0] == 6
+    fht.set_tuning(12, 4, 2, 3)
+    assert fht.get_tuning(12) == (4, 2, 3)
+    assert fht.get_tuning(11) == fht.get_tuning(11)   # other sizes untouched
+    fht.set_tuning(12, None)
+    assert fht.get_tuning(12) == default
+
+
+def test_workspace_follows_the_split(fht, restore):
+    """4096 rows: six levels per pass leave one intermediate level (uint16 for
+    a uint8 image), four levels per pass two (uint16, then int32)."""
+    args = (4096, 4096, fht.LAYOUT_QUADRANT, 0, torch.uint8, torch.int32)
+    fht.set_tuning(12, 6, 1, 1)
+    six = fht.workspace_size(*args)
+    assert six == 4096 * (4096 + 64) * 2
+    fht.set_tuning(12, 4, 1, 1)
+    four = fht.workspace_size(*args)
+    # row pitches rounded up to 64 elements: 4096 + 16 -> 4160, 4096 + 256
+    assert four == 4096 * 4160 * 2 + 4096 * 4352 * 4
+    # 64 rows: one pass of six levels needs no intermediate; 4 + 2 levels do
+    small = (64, 64, fht.LAYOUT_QUADRANT, 0, torch.uint8, torch.int32)
+    fht.set_tuning(6, 6, 1, 1)
+    assert fht.workspace_size(*small) == 0
+    fht.set_tuning(6, 4, 1, 1)
+    assert fht.workspace_size(*small) == 64 * 128 * 2
+
+
+def test_table_is_applied(fht, restore, tmp_path):
+    from paper_1811_06378_gb300 import autotune
+    table = {"table": {"9": {"max_levels": 5, "tile_u8": 3, "tile_wide": 2, "us": 1.0,
+                             "default_us": 2.0},
+                       "13": {"max_levels": 4, "tile_u8": 1, "tile_wide": 3, "us": 1.0,
+                              "default_us": 1.0}}}
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps(table))
+    autotune.load(str(path))
+    assert fht.get_tuning(9) == (5, 3, 2) and fht.get_tuning(13) == (4, 1, 3)
+
+
+def test_shipped_table_is_valid(fht, restore):
+    """The package's own table (if present) names only valid tunings."""
+    import os
+    if not os.path.exists(fht.TUNING_FILE):
+        pytest.skip("no shipped table")
+    res = fht.load_tuning(fht.TUNING_FILE)
+    for k, e in res["table"].items():
+        assert fht.get_tuning(int(k)) == (e["max_levels"], e["tile_u8"], e["tile_wide"])
