@@ -458,7 +458,13 @@ def run_ours(args):
                    "profiled_ms_per_step": prof_total_ms / args.steps,
                    "host_cores": (f"{len(near_cpus)} cores local to the GPU" if near_cpus
                                   else "unbound"),
-                   "launches_per_step": launches_per_step},
+                   "launches_per_step": launches_per_step,
+                   "tuning": {"levels_per_pass_tile_u8_tile_wide":
+                              list(fht.get_tuning(int(math.log2(fht.query_shape(S, S, 0)[0])))),
+                              "table": os.environ.get("FHT_TUNE_FILE",
+                                                      os.path.basename(fht.TUNING_FILE)
+                                                      if os.path.exists(fht.TUNING_FILE)
+                                                      else "none")}},
         "roofline": roofline,
         "gpu_launches": launches,
         "kernels": kernels,
