@@ -96,3 +96,23 @@ def test_8192_rows_four_passes(fht, tuned):
     """2^13 rows at four levels per pass: passes of 4, 3, 3 and 3 levels."""
     img = edges_and_lines(5000, 40, seed=13)
     assert (host(fht.forward(dev(img), 0)) == i32(O.quadrant(img, 0))).all()
+
+
+def test_autotuner_picks_the_fastest_and_sets_it(fht):
+    """A short sweep on one size: the table names the candidate with the
+    smallest summed time, the library is left set to it, and the default's
+    time is reported beside it."""
+    from paper_1811_06378_gb300 import autotune
+    saved = fht.get_tuning(9)
+    try:
+        cands = [(6, 1, 1), (5, 2, 1), (4, 1, 2)]
+        res = autotune.tune(ks=[9], reps=3, warmup=1, candidates=cands)
+        e = res["table"]["9"]
+        times = {tuple(c[:3]): c[3] for c in res["candidates"]["9"]}
+        assert set(times) == set(cands)
+        best = (e["max_levels"], e["tile_u8"], e["tile_wide"])
+        assert times[best] == min(times.values()) == e["us"]
+        assert e["default_us"] == times[(6, 1, 1)]
+        assert fht.get_tuning(9) == best
+    finally:
+        fht.set_tuning(9, *saved)
