@@ -142,13 +142,14 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources; a committed ncu summary is only used while
-    the kernels it measured are unchanged."""
+    """Hash of the library's CUDA and host sources (csrc/; the public header
+    holds declarations and comments only); a committed ncu summary is only
+    used while the code it measured is unchanged."""
     import glob
     import hashlib
     h = hashlib.sha256()
     files = sorted(glob.glob(os.path.join(ROOT, "paper_1811_06378_gb300", "csrc", "*")))
-    for f in files + [os.path.join(ROOT, "include", "fht.h")]:
+    for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())

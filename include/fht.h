@@ -17,9 +17,12 @@
  *
  * Ownership: the caller allocates and frees every device buffer, including
  * the workspace (scratch for intermediate butterfly levels) whose size the
- * *_workspace_size queries return. The library allocates no device memory.
+ * *_workspace_size queries return. The library allocates no device memory at
+ * call time (fht_forward_static's fixed array is part of the loaded library).
  * A workspace may be reused by calls that are ordered on one stream; calls
- * running concurrently need separate workspaces.
+ * running concurrently need separate workspaces. Full-layout calls may run
+ * their quadrants on streams of the library's own, forked from and joined
+ * back into the caller's stream (fht_full_quadrants).
  *
  * Errors: status codes only; nothing is thrown across the ABI.
  *   FHT_EINVAL        bad sizes, pitches, dtypes, slope ranges, null pointers,
