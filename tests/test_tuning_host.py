@@ -82,3 +82,47 @@ def test_shipped_table_is_valid(fht, restore):
     res = fht.load_tuning(fht.TUNING_FILE)
     for k, e in res["table"].items():
         assert fht.get_tuning(int(k)) == (e["max_levels"], e["tile_u8"], e["tile_wide"])
+
+
+def _model_forward_workspace(h, w, q, levels, acc_u16_ok):
+    """Workspace of a forward quadrant plan, modelled from the documented
+    layout: the K levels split into ceil(K / levels) near-equal passes (the
+    larger ones first); every intermediate level keeps the columns
+    x < w_c + 2^k (compact columns), row pitch rounded up to 64 elements,
+    256-byte aligned; uint16 only for the first level of a uint8 image into
+    int32 (exact while it sums at most 2^8 rows), else 4 bytes; levels
+    alternate between two buffers."""
+    hc, wc = (w, h) if q >= 2 else (h, w)
+    n = 1
+    while n < hc:
+        n *= 2
+    K = n.bit_length() - 1
+    W = wc + n
+    if K == 0:
+        return 0
+    P = -(-K // levels)
+    m = [K // P + (1 if p < K % P else 0) for p in range(P)]
+    al = lambda v, a: -(-v // a) * a   # noqa: E731
+    slot = [0, 0]
+    k = 0
+    for p in range(1, P):
+        k += m[p - 1]
+        elem = 2 if (acc_u16_ok and k <= 8 and p == 1) else 4
+        pitch = al(min(W, wc + (1 << k)), 64)
+        slot[(p - 1) % 2] = max(slot[(p - 1) % 2], al(n * pitch * elem, 256))
+    return slot[0] + slot[1]
+
+
+@pytest.mark.parametrize("levels", [4, 5, 6])
+def test_forward_workspace_matches_the_layout_model(fht, restore, levels):
+    """For every split, the library's forward plans take exactly the
+    workspace the documented level layout gives (uint8 into int32 and into
+    float32, all quadrants, 2^1 .. 2^15 rows)."""
+    for K in range(1, 16):
+        fht.set_tuning(K, levels, 1, 1)
+    for h, w in [(1, 1), (3, 40), (100, 300), (700, 90), (1500, 1100), (5000, 40),
+                 (32768, 7), (9, 20000)]:
+        for q in range(4):
+            for acc, u16 in ((torch.int32, True), (torch.float32, False)):
+                got = fht.workspace_size(h, w, fht.LAYOUT_QUADRANT, q, torch.uint8, acc)
+                assert got == _model_forward_workspace(h, w, q, levels, u16), (h, w, q, acc)
