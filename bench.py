@@ -17,9 +17,12 @@ write) before every timed step, W >= 3 warm-up steps. The timed region
 replays the step captured as one CUDA graph (the four quadrants of the
 full-layout calls on four streams); the per-kernel launch times behind the
 roofline come from a second region of the same K steps launched call by call,
-every launch timed alone with the library's per-launch CUDA events. Per-row times, the
-plain single-quadrant forward (the headline FHT at 4096^2 int32) and the
-batched path are reported under "rows".
+every launch timed alone with the library's per-launch CUDA events. The
+roofline is that of the unit of work the dominant kernel serves (one
+quadrant transform or adjoint): its algorithmic bytes (input read once,
+output written once) over the summed time of that unit's kernels. Per-row
+times, the plain single-quadrant forward (the headline FHT at 4096^2 int32)
+and the batched path are reported under "rows".
 
 Rows also include the batched path: 512 uint8 edge maps with sides
 log-uniform in [64, 1024] in one persistent launch, against one fht_forward
@@ -31,9 +34,14 @@ reconstruction.
 Multi-GPU: replicas only (each rank transforms its own image, no collective
 on the data path); value sums all ranks, time is the max over ranks.
 
---impl reference times the CPU oracle (the plain C butterfly + numpy assembly)
-on the host cores, each step the same rows on a power-of-two crop of the image
-sized so that the whole run takes about 90 s.
+cpu_baseline: the CPU oracle (plain C butterfly + numpy assembly, as it
+stands) on one step of the same workload, its independent units (quadrants,
+range quadrants, quadrant adjoints) on a process per host core (up to the
+number of units), and again on one core; nproc and the CPU model recorded.
+
+--impl reference times the same oracle harness on the host cores, each step
+the same rows on a power-of-two crop of the image sized so that the whole run
+takes about 90 s.
 """
 
 from __future__ import annotations
@@ -226,58 +234,219 @@ def dist_setup():
 
 
 # ---------------------------------------------------------------- oracle step
+#
+# The CPU baseline runs the oracle as it stands (test infrastructure, never
+# tuned for this), on the step's independent units: the four quadrants of the
+# full image, the range quadrants and the four quadrant adjoints, each one
+# call of an existing oracle function. With one worker they run one after
+# another; with several, in a process pool (spawned: this process has
+# already initialised CUDA). The image, the gradient and the results live in
+# shared memory, so no array is pickled; the main process assembles the full
+# image (rows by the oracle's row map), applies fhtshift and sums the
+# adjoint's quadrant parts in the order Q0, Q1, Q2, Q3.
 
-def oracle_step(img):
-    """The step's rows by the CPU oracle (test infrastructure, timed only as a
-    baseline)."""
+def _shm_array(name, shape, dtype):
+    from multiprocessing import shared_memory
+    import numpy as np
+    shm = shared_memory.SharedMemory(name=name)
+    return shm, np.ndarray(shape, dtype=dtype, buffer=shm.buf)
+
+
+def _oracle_unit(args):
+    """One unit of the step by the oracle, in a worker (or in-process)."""
     import numpy as np
     import oracle as O
-    h, w = img.shape
-    F = O.full(img)
-    O.fhtshift_full(F, h, w)
-    lo, hi = O.angle_to_slopes(*RANGE_DEG, h, w)
-    for q in range(4):
-        if lo[q] >= 0:
-            O.range_slice(img, q, lo[q], hi[q])
-    g = np.random.default_rng(0).standard_normal(F.shape).astype(np.float32)
-    O.adjoint_full(g, h, w, "f32")
+    kind, q, side, names, lo, hi = args
+    h = w = side
+    R, Wf = O.full_geometry(h, w)
+    shm_i, img = _shm_array(names["img"], (h, w), np.uint8)
+    try:
+        if kind == "full":
+            # quadrant q of the full layout (a square power-of-two image: the
+            # quadrant's own width is the full layout's) into its full rows
+            shm_f, F = _shm_array(names["F"], (R, Wf), np.int64)
+            H = O.quadrant(img, q)
+            for r, (qq, t) in enumerate(O.full_row_map(h, w)):
+                if qq == q:
+                    F[r] = H[t]
+            del F
+            shm_f.close()
+        elif kind == "range":
+            O.range_slice(img, q, lo, hi)
+        else:
+            shm_g, G = _shm_array(names["G"], (R, Wf), np.float32)
+            shm_p, parts = _shm_array(names["parts"], (4, h, w), np.float32)
+            rows = [(r, t) for r, (qq, t) in enumerate(O.full_row_map(h, w)) if qq == q]
+            n, W = O.quadrant_geometry(h, w, q)
+            Gq = np.zeros((n, W), dtype=np.float32)
+            for r, t in rows:
+                Gq[t] = G[r]
+            parts[q] = O.adjoint_quadrant(Gq, h, w, q, "f32")
+            del G, parts
+            shm_g.close()
+            shm_p.close()
+    finally:
+        del img
+        shm_i.close()
+    return kind, q
+
+
+class OracleStep:
+    """The step's rows by the oracle on a side x side edge map (side a power
+    of two), on `workers` processes."""
+
+    def __init__(self, side: int, workers: int):
+        import numpy as np
+        from multiprocessing import shared_memory
+        import oracle as O
+        from workloads import edges_and_lines
+        self.side, self.workers = side, workers
+        h = w = side
+        R, Wf = O.full_geometry(h, w)
+        self.R, self.Wf = R, Wf
+        lo, hi = O.angle_to_slopes(*RANGE_DEG, h, w)
+        self.ranges = [(q, lo[q], hi[q]) for q in range(4) if lo[q] >= 0]
+        self.shm = {}
+        for key, nbytes in (("img", h * w), ("F", R * Wf * 8), ("G", R * Wf * 4),
+                            ("parts", 4 * h * w * 4)):
+            self.shm[key] = shared_memory.SharedMemory(create=True, size=nbytes)
+        self.names = {k: v.name for k, v in self.shm.items()}
+        img = np.ndarray((h, w), np.uint8, buffer=self.shm["img"].buf)
+        img[:] = edges_and_lines(h, w, p_edge=0.05, n_lines=4, seed=4096)
+        G = np.ndarray((R, Wf), np.float32, buffer=self.shm["G"].buf)
+        G[:] = np.random.default_rng(0).standard_normal((R, Wf)).astype(np.float32)
+        del img, G
+        self.pool = None
+        if workers > 1:
+            # an executor, not a Pool: a worker that dies makes the call fail
+            # instead of being restarted for ever
+            import multiprocessing as mp
+            from concurrent.futures import ProcessPoolExecutor
+            self.pool = ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"))
+            # start every worker (interpreter, numpy, oracle library) before timing
+            list(self.pool.map(_warm_worker, range(workers)))
+
+    def units(self):
+        side, names = self.side, self.names
+        jobs = [("full", q, side, names, 0, 0) for q in range(4)]
+        jobs += [("range", q, side, names, lo, hi) for q, lo, hi in self.ranges]
+        jobs += [("adjoint", q, side, names, 0, 0) for q in range(4)]
+        # the largest units first, so that the pool's tail is short
+        return sorted(jobs, key=lambda j: j[0] == "range")
+
+    def run(self):
+        import numpy as np
+        import oracle as O
+        jobs = self.units()
+        if self.pool is not None:
+            list(self.pool.map(_oracle_unit, jobs))
+        else:
+            for j in jobs:
+                _oracle_unit(j)
+        F = np.ndarray((self.R, self.Wf), np.int64, buffer=self.shm["F"].buf)
+        O.fhtshift_full(F, self.side, self.side)
+        parts = np.ndarray((4, self.side, self.side), np.float32, buffer=self.shm["parts"].buf)
+        acc = parts[0].copy()
+        for q in (1, 2, 3):
+            acc = (acc + parts[q]).astype(np.float32)
+        del F, parts
+        return acc
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.shutdown()
+        for v in self.shm.values():
+            v.close()
+            v.unlink()
+
+
+def _warm_worker(_):
+    import oracle as O
+    O.offset(4, 1, 1)
+    return os.getpid()
+
+
+def host_cpu():
+    """Host cores this process may use and the CPU model."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return cores, model or "unknown"
+
+
+def time_oracle_step(side: int, workers: int, reps: int = 1) -> float:
+    """Seconds per oracle step (median of reps) on `workers` processes."""
+    st = OracleStep(side, workers)
+    try:
+        times = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            st.run()
+            times.append(time.perf_counter() - t0)
+    finally:
+        st.close()
+    return statistics.median(times)
 
 
 def cpu_baseline(side: int):
-    from workloads import edges_and_lines
-    img = edges_and_lines(side, side, p_edge=0.05, n_lines=4, seed=4096)
-    t0 = time.perf_counter()
-    oracle_step(img)
-    dt = time.perf_counter() - t0
-    return {"value": side * side / 1e6 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one step (all four rows) on the same {side}x{side} edge map by "
-                      f"the oracle: single-threaded C butterfly + numpy assembly; "
-                      f"{dt:.1f} s"}
+    cores, model = host_cpu()
+    n_units = 4 + 2 + 4
+    workers = max(1, min(cores, n_units))
+    t_all = time_oracle_step(side, workers)
+    t_one = time_oracle_step(side, 1)
+    return {"value": side * side / 1e6 / t_all, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"one step (all four rows) on the same {side}x{side} edge map by the "
+                      f"oracle (plain C butterfly + numpy assembly), its {n_units} independent "
+                      f"units (4 full-image quadrants, 2 range quadrants, 4 adjoint quadrants) "
+                      f"on {workers} worker processes: {t_all:.2f} s",
+            "nproc": cores, "cpu_model": model,
+            "single_core": {"value": side * side / 1e6 / t_one, "unit": UNIT, "cores": 1,
+                            "seconds": t_one}}
 
 
 def run_reference(args):
     ws, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from workloads import edges_and_lines
+    cores, model = host_cpu()
+    workers = max(1, min(cores, 10))
     # size the per-step crop so that warm-up + timed steps stay near 90 s
     budget_s = 90.0
-    probe = edges_and_lines(256, 256, p_edge=0.05, n_lines=4, seed=4096)
-    t0 = time.perf_counter()
-    oracle_step(probe)
-    t256 = time.perf_counter() - t0
+    t256 = time_oracle_step(256, workers)
     crop = 256
     while crop < args.side and (args.steps + args.warmup) * t256 * (2 * crop / 256) ** 2 \
             * math.log2(2 * crop) / 8 <= budget_s:
         crop *= 2
-    img = edges_and_lines(crop, crop, p_edge=0.05, n_lines=4, seed=4096)
-    for _ in range(args.warmup):
-        oracle_step(img)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle_step(img)
-        times.append(time.perf_counter() - t0)
+    st = OracleStep(crop, workers)
+    try:
+        for _ in range(args.warmup):
+            st.run()
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            st.run()
+            times.append(time.perf_counter() - t0)
+    finally:
+        st.close()
     ms = 1e3 * sum(times) / len(times)
     value = crop * crop / 1e6 / (ms / 1e3)
     line = {
@@ -288,8 +457,10 @@ def run_reference(args):
         "config": {"workload": f"{args.side}x{args.side} u8 edge map (5% edges + 4 lines): "
                                "full 4-quadrant image, fhtshift, [-15,15] deg range, "
                                "FP32 full adjoint", "sample_crop": f"{crop}x{crop}"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step = all rows on a {crop}x{crop} crop"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": f"each step = all rows on a {crop}x{crop} crop, its 10 "
+                                   f"independent units on {workers} worker processes",
+                         "nproc": cores, "cpu_model": model},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -420,26 +591,73 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     rows = {}   # filled by the per-row section below
 
-    # ---- roofline of the dominant kernel (largest share of the profiled
-    # step): the library's CUDA events on the launch stream give its launch
-    # times, and its algorithmic bytes per launch (the level it reads as
-    # stored plus the level it writes, from the launch geometry)
+    # ---- roofline. The dominant kernel is the one with the largest share of
+    # the profiled step. It serves a unit of the step's work -- one quadrant
+    # transform, one quadrant adjoint, the range transform of one quadrant,
+    # the fhtshift of the full image -- whose algorithmic bytes are fixed by
+    # the transform's definition: the input read once and the output written
+    # once (h*w*in_bytes + n*W*4 per quadrant; n*W*4 + h*w*4 per quadrant
+    # adjoint). achieved = those bytes / the summed time of all the kernels
+    # of that unit (their per-launch CUDA-event times, each launch alone).
+    # The pass-counted figure (the level each launch reads as stored plus
+    # the level it writes, over that launch's time) is kept beside it.
+    nq, Wq = fht.query_shape(S, S, 0)   # every quadrant of the square full layout
+    rng_rows = sum(t.shape[0] for t in rng_out.values())
+    families = {
+        "adjoint quadrant (FP32 gradient -> image gradient)": (
+            lambda k: k.startswith("adjoint_fused"), 4, nq * Wq * 4 + S * S * 4),
+        "forward quadrant (uint8 -> int32)": (
+            lambda k: k.startswith("forward_fused") and not k.endswith("_range"), 4,
+            S * S + nq * Wq * 4),
+        "range quadrant (uint8 -> int32 slopes of [-15, 15] deg)": (
+            lambda k: k.endswith("_range"), len(used),
+            (len(used) * S * S + rng_rows * Wq * 4) / max(len(used), 1)),
+        "fhtshift of the full image": (lambda k: k.startswith("fhtshift"), 1, 2 * R * Wf * 4),
+    }
+    steps = args.steps
+    units = {}
+    for fam, (match, per_step, unit_bytes) in families.items():
+        ks = [k for k in prof if match(k)]
+        if not ks:
+            continue
+        fam_ms = sum(prof[k][1] for k in ks) / steps          # per step
+        unit_ms = fam_ms / per_step
+        traffic_parts = [traffic_per_launch(k, S) for k in ks]
+        traffic = None
+        if all(t is not None for t in traffic_parts):
+            traffic = sum(t * prof[k][0] / steps for t, k in zip(traffic_parts, ks)) / per_step
+        units[fam] = {"kernels": ks, "units_per_step": per_step,
+                      "alg_bytes_per_unit": unit_bytes, "unit_ms": unit_ms,
+                      "achieved_gbs": unit_bytes / (unit_ms / 1e3) / 1e9,
+                      "frac": unit_bytes / (unit_ms / 1e3) / 1e9 / peak,
+                      "dram_bytes_per_unit": traffic}
     dom_name, (dom_launches, dom_ms, dom_bytes) = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_fam = next((f for f, v in units.items() if dom_name in v["kernels"]), None)
     avg_ms = dom_ms / max(dom_launches, 1)
-    bytes_per_launch = dom_bytes / max(dom_launches, 1)
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    traffic = traffic_per_launch(dom_name, S)
+    pass_bytes = dom_bytes / max(dom_launches, 1)
+    pass_frac = pass_bytes / (avg_ms / 1e3) / 1e9 / peak
+    if dom_fam is not None:
+        u = units[dom_fam]
+        achieved, frac, traffic = u["achieved_gbs"], u["frac"], u["dram_bytes_per_unit"]
+        unit_note = dom_fam
+    else:   # a kernel outside the step's units (not expected): its own launch
+        achieved, frac, traffic = pass_bytes / (avg_ms / 1e3) / 1e9, pass_frac, None
+        unit_note = "one launch (pass-counted bytes)"
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-        "frac": achieved / peak, "traffic": traffic,
+        "frac": frac, "traffic": traffic,
         "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-        "kernel": dom_name, "launches_profiled": dom_launches,
-        "avg_launch_ms": avg_ms, "alg_bytes_per_launch": bytes_per_launch,
-        "share_of_step": dom_ms / prof_total_ms,
+        "kernel": dom_name, "share_of_step": dom_ms / prof_total_ms,
+        "unit_of_work": unit_note,
+        "accounting": "algorithmic bytes of one unit (input read once, output written "
+                      "once) over the summed per-launch times of that unit's kernels; "
+                      "traffic = ncu DRAM read+write bytes of those kernels per unit",
+        "launches_profiled": dom_launches, "avg_launch_ms": avg_ms,
+        "frac_pass_counted": pass_frac, "pass_bytes_per_launch": pass_bytes,
     }
     kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / max(v[0], 1),
-                   "alg_bytes_per_launch": v[2] / max(v[0], 1),
-                   "achieved_gbs": (v[2] / max(v[0], 1)) / (v[1] / max(v[0], 1) / 1e3) / 1e9,
+                   "pass_bytes_per_launch": v[2] / max(v[0], 1),
+                   "pass_gbs": (v[2] / max(v[0], 1)) / (v[1] / max(v[0], 1) / 1e3) / 1e9,
                    "share_of_step": v[1] / prof_total_ms} for k, v in prof.items()}
 
     line = {
@@ -468,6 +686,7 @@ def run_ours(args):
                                                       else "none")}},
         "roofline": roofline,
         "gpu_launches": launches,
+        "units": units,
         "kernels": kernels,
         "rows": rows,
         "clocks": clk,

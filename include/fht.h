@@ -186,7 +186,9 @@ fht_status fhtshift(const void *in, void *out, fht_dtype dtype, int h, int w,
  * image up to 4096 x 4096 into int32 fits, with the default tuning).
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.
+ * before any stream capture. A context that is torn down and created again
+ * (cudaDeviceReset) holds the array at a new address: the first call in the
+ * new context looks it up again, so it too should come before any capture.
  * Sharing: all calls on a device share the one array, which keeps the last
  * call's contents (nothing in it needs to start at zero). Calls whose kernels
  * overlap on the GPU race on it: issue them in order on one stream. */
@@ -260,7 +262,7 @@ fht_status fht_row_argmax(const void *hough, fht_dtype dtype, int rows, int cols
 
 /* ------------------------------------------------------------ sheared (Section 4)
  * The paper's way to a chosen range of line angles: shear the image
- * horizontally by spl ("shift per line") inside the first butterfly
+ * horizontally by spl (the shift per line) inside the first butterfly
  * iteration, then run one quadrant. Row y of the image (of the transposed
  * image for Q2/Q3) is taken as rotated right by s(y) = floor(y*spl + 1/2)
  * columns modulo W (the paper fixes no rounding; it is evaluated exactly with
@@ -362,9 +364,12 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
  * `stream`, all capturable in a CUDA graph. The descriptors are staged in
  * pinned host memory owned by the plan: three tables used in turn by direct
  * calls (a call first waits until the copy of the call that used its table
- * last has run) and one for the latest capture (a graph replays the
- * descriptors given when it was captured until the plan is captured again).
- * A plan serves one stream at a time. */
+ * last has run), and one more table for every stream capture, allocated by
+ * the capturing call and kept until fht_plan_destroy, so that each graph
+ * replays the descriptors given when it was captured, whatever the plan runs
+ * or captures later (each capture holds a few hundred bytes per pass of every
+ * image; FHT_ENOMEM if that table cannot be allocated). A plan serves one
+ * stream at a time. */
 fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void *workspace,
                                size_t workspace_bytes, void *stream);
 
@@ -404,15 +409,12 @@ fht_status fht_batched_test_hooks(fht_plan *plan, long long wait_budget_cycles, 
 void fht_plan_destroy(fht_plan *plan);
 
 /* Device status of the single-image transforms (fht_forward,
- * fht_forward_range, fht_full_quadrants, fht_adjoint and fht_forward_static)
- * when their two-block passes run as persistent pipelined kernels (set
- * FHT_PIPE=1 in the environment before the library loads; off by default),
- * whose two warp groups hand shared tiles to each other through bounded
- * waits. Without it the status is always FHT_OK. Waits for every launch
- * issued so far in this process, then returns FHT_ETIMEOUT if any such wait
- * ran out of its clock budget (about a second; the launch then ended early
- * and its output is incomplete) and resets the count, else FHT_OK; FHT_ECUDA
- * if the device could not be synchronised. Not in the paper. */
+ * fht_forward_range, fht_full_quadrants, fht_adjoint and fht_forward_static).
+ * Waits for every launch issued so far in this process, then returns
+ * FHT_ETIMEOUT if any kernel recorded a device-side error since the last call
+ * (the count is then reset), else FHT_OK; FHT_ECUDA if the device could not
+ * be synchronised. The release build's kernels record none, so there the
+ * status is FHT_OK whenever the device synchronises. Not in the paper. */
 fht_status fht_device_status(void);
 
 /* ------------------------------------------------------------ tuning

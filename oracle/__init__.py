@@ -41,10 +41,11 @@ with gcc, no fast-math). Readings of points the paper leaves open:
 7. Angle ranges map to slopes by t = (n-1)*tan(theta); see ``angle_to_slopes``.
 8. The shear of Section 4 (``sheared_quadrant``): row y of the (transposed)
    image is shifted cyclically right by s(y) = floor(y*spl + 1/2) columns
-   (spl = "shift per line"; the paper gives no rounding), evaluated exactly
+   (spl, the shift per line; the paper gives no rounding), evaluated exactly
    with spl in fixed point (32 fractional bits, rounded half up), then the plain
    quadrant transform runs on the cyclic width W = w + n, which the paper
-   keeps ("the black zone will simply move").
+   keeps (Section 4: the black zone only moves, nothing wraps into the
+   meaningful zone).
 """
 
 from __future__ import annotations

@@ -569,8 +569,8 @@ def launch_count() -> int:
 
 
 def device_status() -> int:
-    """Wait for the device; FHT_ETIMEOUT if a pipelined pass ran out of its
-    wait budget since the last call (the count is reset), else FHT_OK."""
+    """Wait for the device; FHT_ETIMEOUT if a kernel recorded a device-side
+    error since the last call (the count is reset), else FHT_OK."""
     return int(lib.fht_device_status())
 
 

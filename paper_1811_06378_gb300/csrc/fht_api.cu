@@ -259,14 +259,10 @@ cudaError_t launch_forward_op(int M, const PassDesc &d, int acc, int op, cudaStr
 
 // Block-A warp-columns per tile: wider tiles compute less halo but need more
 // shared memory (fewer CTAs per SM). Overridable for tuning through
-// FHT_TUNE="n_a_u16,n_a_wide"; FHT_PIPE=1 runs two-block passes as the
-// persistent warp-specialised pipeline instead of one item per CTA. The
-// pipeline is off by default: block B costs about 1.5x block A, so its
-// consumer warps bound it (4096^2 final int32 pass: 87 us against 72 us).
+// FHT_TUNE="n_a_u16,n_a_wide".
 struct Tune {
     int n_a_u16 = 1;    // first pass over uint8 images (uint16 shared tile)
     int n_a_wide = 1;   // 4-byte shared tiles
-    bool pipe = false;
     bool staged = true;
     bool concurrent = true;
     Tune() {
@@ -277,7 +273,6 @@ struct Tune {
                 n_a_wide = b;
             }
         }
-        if (const char *e = getenv("FHT_PIPE")) pipe = e[0] == '1' && e[1] == 0;
         if (const char *e = getenv("FHT_STAGED")) staged = !(e[0] == '0' && e[1] == 0);
         if (const char *e = getenv("FHT_CONCURRENT")) concurrent = !(e[0] == '0' && e[1] == 0);
     }
@@ -310,7 +305,6 @@ std::vector<unsigned int (*)()> &counter_fns() {
 
 namespace fht {
 
-bool pipe_enabled() { return g_tune.pipe; }
 bool staged_enabled() { return g_tune.staged; }
 
 bool register_device_counter(unsigned int (*read_and_reset)()) {

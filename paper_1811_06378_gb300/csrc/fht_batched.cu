@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -42,11 +43,16 @@ struct Table {
     size_t table_bytes = 0, counters_off = 0, done_off = 0, levels_off = 0;
     size_t ws_bytes = 0, smem = 0;
     // kDirectTables copies used in turn by direct launches (each reused only
-    // once its previous copy has run), then one for the latest stream capture
+    // once its previous copy has run); the segments as built, without
+    // pointers, follow them (the template a capture's own table starts from)
     void *host_table = nullptr;
     cudaEvent_t copied[kDirectTables] = {};
     bool copy_pending[kDirectTables] = {};
     int next_table = 0;
+    // one pinned table per stream capture, kept until the plan is destroyed:
+    // a captured graph's copy node reads its own table at every replay, so a
+    // later capture (or direct call) never changes what an earlier graph runs
+    std::vector<void *> capture_tables;
 };
 
 void release_table(Table &T) {
@@ -58,6 +64,33 @@ void release_table(Table &T) {
     }
     if (T.host_table) cudaFreeHost(T.host_table);
     T.host_table = nullptr;
+    for (void *p : T.capture_tables) cudaFreeHost(p);
+    T.capture_tables.clear();
+}
+
+// A new pinned table for a stream capture, copied from the template. The
+// capture is in progress on this thread: the allocation (no stream work) is
+// made in the relaxed capture mode, which lets it proceed without ending the
+// capture, and the caller's mode is restored afterwards.
+void *new_capture_table(Table &T) {
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    if (cudaThreadExchangeStreamCaptureMode(&mode) != cudaSuccess) return nullptr;
+    void *p = nullptr;
+    const cudaError_t e = cudaMallocHost(&p, T.counters_off);
+    cudaThreadExchangeStreamCaptureMode(&mode);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    try {
+        T.capture_tables.push_back(p);
+    } catch (...) {
+        cudaFreeHost(p);
+        return nullptr;
+    }
+    std::memcpy(p, static_cast<unsigned char *>(T.host_table) + kDirectTables * T.counters_off,
+                T.table_bytes);
+    return p;
 }
 
 }  // namespace
@@ -297,17 +330,20 @@ fht_status launch_table(fht_plan *plan, Table &T, const CallPtrs *calls, Kernel 
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FHT_ECUDA;
     const bool capturing = cs != cudaStreamCaptureStatusNone;
     // a direct launch takes the next table of the ring, once the copy of the
-    // launch that used it last has read it
-    const int tab = capturing ? kDirectTables : T.next_table;
-    if (!capturing) {
+    // launch that used it last has read it; a capture gets a table of its own
+    const int tab = T.next_table;
+    unsigned char *table = nullptr;
+    if (capturing) {
+        table = static_cast<unsigned char *>(new_capture_table(T));
+        if (!table) return FHT_ENOMEM;
+    } else {
         T.next_table = (T.next_table + 1) % kDirectTables;
         if (T.copy_pending[tab]) {
             if (cudaEventSynchronize(T.copied[tab]) != cudaSuccess) return FHT_ECUDA;
             T.copy_pending[tab] = false;
         }
+        table = static_cast<unsigned char *>(T.host_table) + (size_t)tab * T.counters_off;
     }
-    unsigned char *table = static_cast<unsigned char *>(T.host_table) +
-                           (size_t)tab * T.counters_off;
     BatchSeg *segs = reinterpret_cast<BatchSeg *>(table);
     for (int i = 0; i < T.n_segs; ++i) {
         BatchSeg &sg = segs[i];

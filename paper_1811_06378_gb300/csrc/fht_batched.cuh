@@ -59,10 +59,12 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     return v;
 }
 
+// Sources are read with coherent loads (NC = false): a second pass reads the
+// level its image's first pass wrote earlier in this same launch.
 template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
 __device__ __forceinline__ void run_item(const PassDesc &d, int gy, int tile, unsigned char *sm) {
-    fused_forward_item<MA, MB, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(
+    fused_forward_item<MA, MB, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, 0, false>(
         d, gy, tile, reinterpret_cast<MidE *>(sm));
 }
 

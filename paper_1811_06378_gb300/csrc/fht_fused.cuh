@@ -96,18 +96,32 @@ __device__ __noinline__ void store8_edge(E *row, int lo, int cols, Vec8<Acc> v) 
     }
 }
 
+// One aligned vector load. NC (the default) reads through the non-coherent
+// read-only path (ld.global.nc), which CUDA allows only for data that no
+// thread writes during the kernel: the caller's images and gradients, and
+// levels written by an earlier launch. A level written earlier in the same
+// launch (the persistent batched kernel, whose passes hand levels to each
+// other through its dependency counters) must be read with NC = false: a
+// plain, coherent load, ordered after the producer's release by the
+// consumer's acquire.
+template <bool NC, typename V>
+__device__ __forceinline__ V ldvec(const V *p) {
+    if constexpr (NC) return __ldg(p);
+    else return *p;
+}
+
 // v[k] = row[lo + k] for k < 8; all 8 must lie inside the row. The aligned
 // granules covering them are loaded whole; the start offset inside the first
 // granule selects the elements with selects and byte permutes (no branches,
 // so the loads of several rows can all be in flight together).
-template <typename E, typename Acc>
+template <typename E, typename Acc, bool NC = true>
 __device__ __forceinline__ void load8_fast(const E *row, int lo, Acc (&v)[kV]) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(row + lo);
     if constexpr (sizeof(E) == 1) {
         const int delta = (int)(a & 7);
         const uint2 *g = reinterpret_cast<const uint2 *>(a & ~(uintptr_t)7);
-        uint2 q0 = __ldg(g), q1 = make_uint2(0, 0);
-        if (delta) q1 = __ldg(g + 1);
+        uint2 q0 = ldvec<NC>(g), q1 = make_uint2(0, 0);
+        if (delta) q1 = ldvec<NC>(g + 1);
         const uint32_t w0 = q0.x, w1 = q0.y, w2 = q1.x, w3 = q1.y;
         const bool hi = delta >= 4;
         const uint32_t u0 = hi ? w1 : w0, u1 = hi ? w2 : w1, u2 = hi ? w3 : w2;
@@ -121,8 +135,8 @@ __device__ __forceinline__ void load8_fast(const E *row, int lo, Acc (&v)[kV]) {
     } else if constexpr (sizeof(E) == 2) {
         const int delta = (int)((a & 15) >> 1);
         const uint4 *g = reinterpret_cast<const uint4 *>(a & ~(uintptr_t)15);
-        uint4 q0 = __ldg(g), q1 = make_uint4(0, 0, 0, 0);
-        if (delta) q1 = __ldg(g + 1);
+        uint4 q0 = ldvec<NC>(g), q1 = make_uint4(0, 0, 0, 0);
+        if (delta) q1 = ldvec<NC>(g + 1);
         const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
         const int j = delta >> 1;
         uint32_t u[5];
@@ -139,8 +153,8 @@ __device__ __forceinline__ void load8_fast(const E *row, int lo, Acc (&v)[kV]) {
     } else {
         const int delta = (int)((a & 15) >> 2);
         const uint4 *g = reinterpret_cast<const uint4 *>(a & ~(uintptr_t)15);
-        uint4 q0 = __ldg(g), q1 = __ldg(g + 1), q2 = make_uint4(0, 0, 0, 0);
-        if (delta) q2 = __ldg(g + 2);
+        uint4 q0 = ldvec<NC>(g), q1 = ldvec<NC>(g + 1), q2 = make_uint4(0, 0, 0, 0);
+        if (delta) q2 = ldvec<NC>(g + 2);
         const uint32_t w[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y,
                                 q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
         using IsF = std::integral_constant<bool, std::is_same<Acc, float>::value &&
@@ -152,10 +166,10 @@ __device__ __forceinline__ void load8_fast(const E *row, int lo, Acc (&v)[kV]) {
 }
 
 // v[k] = row[lo + k] for k < 8, zero outside [0, cols).
-template <typename E, typename Acc>
+template <typename E, typename Acc, bool NC = true>
 __device__ __forceinline__ void load8(const E *row, int lo, int cols, Acc (&v)[kV]) {
     if (lo >= 0 && lo + kV <= cols) {
-        load8_fast<E, Acc>(row, lo, v);
+        load8_fast<E, Acc, NC>(row, lo, v);
     } else {
         const Vec8<Acc> r = load8_edge<E, Acc>(row, lo, cols);
 #pragma unroll
@@ -164,7 +178,7 @@ __device__ __forceinline__ void load8(const E *row, int lo, int cols, Acc (&v)[k
 }
 
 // Cyclic variant: v[k] = row[(lo + k) mod W] (gradients have no zero zone).
-template <typename E, typename Acc>
+template <typename E, typename Acc, bool NC = true>
 __device__ __forceinline__ void load8_cyclic(const E *row, int lo, int W, Acc (&v)[kV]) {
     int c = lo;
     if (c < 0 || c >= W) {
@@ -172,7 +186,7 @@ __device__ __forceinline__ void load8_cyclic(const E *row, int lo, int W, Acc (&
         if (c < 0) c += W;
     }
     if (c + kV <= W) {
-        load8<E, Acc>(row, c, W, v);
+        load8<E, Acc, NC>(row, c, W, v);
         return;
     }
 #pragma unroll
@@ -305,7 +319,7 @@ __host__ __device__ inline TileGeom tile_geom(int MA, int MB, int n_a, int nwarp
 
 // Source row segment for block A: 8 buffer columns starting at i0 of buffer
 // row s, into v (buffer order).
-template <int SG, bool ADJ, typename Acc, typename SrcE>
+template <int SG, bool ADJ, typename Acc, typename SrcE, bool NC = true>
 __device__ __forceinline__ void load_source(const PassDesc &d, int M, int S, int a, int s,
                                             int A_off, int i0, Acc (&v)[kV]) {
     constexpr int sg = SG;
@@ -323,19 +337,19 @@ __device__ __forceinline__ void load_source(const PassDesc &d, int M, int S, int
                 return;
             }
             row = d.src_row_base + d.src_row_dir * row;
-            load8_cyclic<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, col, d.W, v);
+            load8_cyclic<SrcE, Acc, NC>(base + (int64_t)row * d.lo.pitch, col, d.W, v);
         } else {
             if (row >= d.lo.rows) {
 #pragma unroll
                 for (int k = 0; k < kV; ++k) v[k] = Acc(0);
                 return;
             }
-            load8<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, col, d.lo.cols, v);
+            load8<SrcE, Acc, NC>(base + (int64_t)row * d.lo.pitch, col, d.lo.cols, v);
         }
     } else {
         const int row = ((S * (1 << M) + s) << d.k0) + a;
-        if constexpr (ADJ) load8_cyclic<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, lo, d.W, v);
-        else load8<SrcE, Acc>(base + (int64_t)row * d.lo.pitch, lo, d.lo.cols, v);
+        if constexpr (ADJ) load8_cyclic<SrcE, Acc, NC>(base + (int64_t)row * d.lo.pitch, lo, d.W, v);
+        else load8<SrcE, Acc, NC>(base + (int64_t)row * d.lo.pitch, lo, d.lo.cols, v);
     }
     if (sg < 0) reverse8(v);
 }
@@ -343,7 +357,7 @@ __device__ __forceinline__ void load_source(const PassDesc &d, int M, int S, int
 // Transposed image block for block A of the first pass (quadrants Q2, Q3):
 // rows s0..s0+RA-1 of the transposed image are image columns; the 8 buffer
 // columns are 8 image rows.
-template <int SG, int RA, typename Acc, typename SrcE>
+template <int SG, int RA, typename Acc, typename SrcE, bool NC = true>
 __device__ __forceinline__ void load_source_transposed(const PassDesc &d, int M, int S,
                                                        int s0, int A_off, int i0,
                                                        Acc (&v)[RA][kV]) {
@@ -357,7 +371,7 @@ __device__ __forceinline__ void load_source_transposed(const PassDesc &d, int M,
     for (int k = 0; k < kV; ++k) {
         const int c = lo + k;   // image row
         if (c >= 0 && c < d.lo.cols) {
-            load8<SrcE, Acc>(img + (int64_t)c * d.lo.pitch, y0, d.lo.rows, blk[k]);
+            load8<SrcE, Acc, NC>(img + (int64_t)c * d.lo.pitch, y0, d.lo.rows, blk[k]);
         } else {
 #pragma unroll
             for (int j = 0; j < kV; ++j) blk[k][j] = Acc(0);
@@ -379,15 +393,16 @@ struct Block {
 
 // Rare edge items (tile borders, image borders, wraps): per-row checked loads,
 // out of line.
-template <int SG, int RA, bool ADJ, typename Acc, typename SrcE>
+template <int SG, int RA, bool ADJ, typename Acc, typename SrcE, bool NC = true>
 __device__ __noinline__ Block<Acc, RA> load_block_a_edge(const PassDesc &d, int M, int S, int a,
                                                          int s0, int A_off, int i0) {
     Block<Acc, RA> b;
     if (!ADJ && d.lo_image && d.transpose) {
-        load_source_transposed<SG, RA, Acc, SrcE>(d, M, S, s0, A_off, i0, b.x);
+        load_source_transposed<SG, RA, Acc, SrcE, NC>(d, M, S, s0, A_off, i0, b.x);
     } else {
 #pragma unroll
-        for (int r = 0; r < RA; ++r) load_source<SG, ADJ, Acc, SrcE>(d, M, S, a, s0 + r, A_off, i0, b.x[r]);
+        for (int r = 0; r < RA; ++r)
+            load_source<SG, ADJ, Acc, SrcE, NC>(d, M, S, a, s0 + r, A_off, i0, b.x[r]);
     }
     return b;
 }
@@ -421,7 +436,7 @@ __device__ __noinline__ Vec8<Acc> load8_sheared_edge(const PassDesc &d, const Sr
 // row0 + r (an image column for the transposed quadrants) rotated right by
 // its shear shift, cyclically on W, zero outside the image; this lane's 8
 // ascending columns start at X (buffer order after the reverse for sign -1).
-template <int SG, int RA, typename Acc, typename SrcE>
+template <int SG, int RA, typename Acc, typename SrcE, bool NC = true>
 __device__ __forceinline__ void load_block_a_sheared(const PassDesc &d, int row0, int X,
                                                      int Xw0, int Xw1, Acc (&v)[RA][kV]) {
     const SrcE *img = reinterpret_cast<const SrcE *>(d.lo.ptr);
@@ -436,7 +451,7 @@ __device__ __forceinline__ void load_block_a_sheared(const PassDesc &d, int row0
             const SrcE *p0 = img + (int64_t)row0 * d.lo.pitch;
 #pragma unroll
             for (int r = 0; r < RA; ++r) {
-                load8_fast<SrcE, Acc>(p0 + r * d.lo.pitch, X - shear_shift(d, row0 + r), v[r]);
+                load8_fast<SrcE, Acc, NC>(p0 + r * d.lo.pitch, X - shear_shift(d, row0 + r), v[r]);
                 if constexpr (SG < 0) reverse8(v[r]);
             }
             return;
@@ -452,7 +467,7 @@ __device__ __forceinline__ void load_block_a_sheared(const PassDesc &d, int row0
         }
         const int c0 = wrap_w(X - shear_shift(d, y), d.W);
         if (!d.transpose && c0 + kV <= d.W) {
-            load8<SrcE, Acc>(img + (int64_t)y * d.lo.pitch, c0, d.lo.cols, v[r]);
+            load8<SrcE, Acc, NC>(img + (int64_t)y * d.lo.pitch, c0, d.lo.cols, v[r]);
         } else {
             const Vec8<Acc> e = load8_sheared_edge<Acc, SrcE>(d, img, y, c0);
 #pragma unroll
@@ -466,7 +481,7 @@ __device__ __forceinline__ void load_block_a_sheared(const PassDesc &d, int row0
 // Whether every row and every lane of the warp item (columns wbase ..
 // wbase + 255) lies inside the source is decided once, warp-uniformly; the
 // common interior case then issues all rows' loads without branches.
-template <int SG, int RA, bool ADJ, typename Acc, typename SrcE>
+template <int SG, int RA, bool ADJ, typename Acc, typename SrcE, bool NC = true>
 __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, int a, int s0,
                                              int A_off, int wbase, int i0, Acc (&v)[RA][kV]) {
     constexpr int sg = SG;
@@ -478,8 +493,8 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
             const int X = (sg > 0 ? p_first : p_first - (kV - 1)) - splus;
             // ascending columns of the whole warp item: [Xw0, Xw1)
             const int Xw0 = sg > 0 ? A_off + wbase - splus : A_off - wbase - (32 * kV - 1);
-            load_block_a_sheared<SG, RA, Acc, SrcE>(d, S * (1 << M) + s0, X, Xw0, Xw0 + 32 * kV,
-                                                    v);
+            load_block_a_sheared<SG, RA, Acc, SrcE, NC>(d, S * (1 << M) + s0, X, Xw0,
+                                                        Xw0 + 32 * kV, v);
             return;
         }
         if (!d.lo_image && d.lo_win) {
@@ -498,7 +513,7 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
                 const int lo = sg > 0 ? p_first : p_first - (kV - 1);
                 int j = wrap_w(lo - win_base(d, (S << M) + sp, a), d.W);
                 if (j >= d.win_len) j = 0;
-                load8_fast<SrcE, Acc>(p0 + r * stride, j, v[r]);
+                load8_fast<SrcE, Acc, NC>(p0 + r * stride, j, v[r]);
                 if constexpr (sg < 0) reverse8(v[r]);
             }
             return;
@@ -530,7 +545,8 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
         interior = lo_min >= 0 && hi_max <= (ADJ ? d.W : d.lo.cols);
     }
     if (!interior) {
-        const Block<Acc, RA> b = load_block_a_edge<SG, RA, ADJ, Acc, SrcE>(d, M, S, a, s0, A_off, i0);
+        const Block<Acc, RA> b =
+            load_block_a_edge<SG, RA, ADJ, Acc, SrcE, NC>(d, M, S, a, s0, A_off, i0);
 #pragma unroll
         for (int r = 0; r < RA; ++r)
 #pragma unroll
@@ -544,7 +560,7 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
         Acc blk[kV][kV];
 #pragma unroll
         for (int k = 0; k < kV; ++k)
-            load8_fast<SrcE, Acc>(base + (int64_t)(lo + k) * d.lo.pitch, row0, blk[k]);
+            load8_fast<SrcE, Acc, NC>(base + (int64_t)(lo + k) * d.lo.pitch, row0, blk[k]);
 #pragma unroll
         for (int r = 0; r < RA; ++r)
 #pragma unroll
@@ -577,7 +593,7 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
     const SrcE *p0 = base + first_row * d.lo.pitch;
 #pragma unroll
     for (int r = 0; r < RA; ++r) {
-        load8_fast<SrcE, Acc>(p0 + r * stride, lo0 + r * dlo, v[r]);
+        load8_fast<SrcE, Acc, NC>(p0 + r * stride, lo0 + r * dlo, v[r]);
         if constexpr (sg < 0) reverse8(v[r]);
     }
 }
@@ -997,7 +1013,7 @@ __device__ __forceinline__ ItemPos item_pos(const PassDesc &d, int T, int gy, in
 // mini-strips of RA source rows, run MA levels in registers and write the
 // results to the shared tile sm (nothing to do for a black tile).
 template <int MA, int MB, int SG, bool ADJ, typename Acc, typename SrcE, typename MidE,
-          int OP = 0>
+          int OP = 0, bool NC = true>
 __device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &G,
                                              const ItemPos &ip, MidE *sm, int warp, int nwarps,
                                              int lane) {
@@ -1010,8 +1026,8 @@ __device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &
         const int g = item % RB, wc = item / RB;
         const int i0 = wc * kWarpValid + lane * kV;
         Acc v[RA][kV];
-        load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, ip.S, ip.a, g * RA, ip.A_off, wc * kWarpValid,
-                                             i0, v);
+        load_block_a<SG, RA, ADJ, Acc, SrcE, NC>(d, M, ip.S, ip.a, g * RA, ip.A_off,
+                                                 wc * kWarpValid, i0, v);
         reg_butterfly<MA, Acc, OP>(v);
         if (lane < kLanesValid) {
             const int pos = (8 + PAD) * (i0 >> 3);   // i0 is a multiple of 8
@@ -1107,9 +1123,11 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
 // none of its code; FIN likewise selects the destination (0 an intermediate
 // level, 1 the caller's layout, 2 an adjoint's transposed image gradient), so
 // each kernel holds one store path. OP is the operation along the patterns
-// (Combine: 0 the sum, 1 the maximum, 2 the minimum).
+// (Combine: 0 the sum, 1 the maximum, 2 the minimum). NC = false reads the
+// source through coherent loads (a level written earlier in the same launch;
+// see ldvec).
 template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
-          typename DstE, int OP = 0>
+          typename DstE, int OP = 0, bool NC = true>
 __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm) {
     constexpr int M = MA + MB, RA = 1 << MA;
     constexpr int PAD = TilePad<MidE>::kPad;
@@ -1125,8 +1143,8 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             const int i0 = item * kWarpValid + lane * kV;
             Acc v[RA][kV];
             if (!ip.black) {
-                load_block_a<SG, RA, ADJ, Acc, SrcE>(d, M, ip.S, ip.a, 0, ip.A_off,
-                                                     item * kWarpValid, i0, v);
+                load_block_a<SG, RA, ADJ, Acc, SrcE, NC>(d, M, ip.S, ip.a, 0, ip.A_off,
+                                                         item * kWarpValid, i0, v);
                 reg_butterfly<MA, Acc, OP>(v);
             } else {
 #pragma unroll
@@ -1147,7 +1165,7 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
             }
         }
     } else {
-        tile_block_a<MA, MB, SG, ADJ, Acc, SrcE, MidE, OP>(d, G, ip, sm, warp, nwarps, lane);
+        tile_block_a<MA, MB, SG, ADJ, Acc, SrcE, MidE, OP, NC>(d, G, ip, sm, warp, nwarps, lane);
         if (!ip.black) __syncthreads();   // black is the same for the whole CTA
         tile_block_b<MA, MB, SG, ADJ, FIN, Acc, MidE, DstE, OP>(d, G, ip, sm, warp, nwarps, lane);
     }

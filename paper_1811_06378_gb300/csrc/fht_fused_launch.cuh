@@ -8,7 +8,6 @@
 
 #include "fht_fused.cuh"
 #include "fht_host.h"
-#include "fht_pipe.cuh"
 #include "fht_staged.cuh"
 
 namespace fht {
@@ -24,6 +23,14 @@ constexpr size_t kMaxTileSmem = 227 * 1024;
 // Bytes a pass must read and write at least: its source level as stored
 // (image, or compact intermediate rows of the launched groups) and its
 // destination (intermediate rows, output slopes, or image gradient).
+// Whether a pass computes only part of its slopes (range pruning): forward
+// launches of such passes are named with a "_range" suffix so that
+// per-launch timings of range transforms and of whole quadrants can be told
+// apart.
+inline bool pass_pruned(const PassDesc &d, int M) {
+    return d.need_lo != 0 || d.need_hi != (1 << (d.k0 + M)) - 1;
+}
+
 inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t dst_bytes) {
     const double rows = (double)d.s_count * d.a_count * (1 << M);
     double rd, wr;
@@ -78,57 +85,6 @@ __global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
         d, blockIdx.y, blockIdx.x, reinterpret_cast<MidE *>(smem_raw));
 }
 
-namespace {
-// Waits of the pipelined kernels in this translation unit that ran out of
-// their clock budget (read and reset by fht_device_status).
-__device__ unsigned int g_pipe_timeouts = 0;
-
-unsigned int read_reset_pipe_timeouts() {
-    unsigned int v = 0;
-    const unsigned int zero = 0;
-    if (cudaMemcpyFromSymbol(&v, g_pipe_timeouts, sizeof v) != cudaSuccess ||
-        cudaMemcpyToSymbol(g_pipe_timeouts, &zero, sizeof zero) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return v;
-}
-
-const bool g_pipe_counter_registered = register_device_counter(&read_reset_pipe_timeouts);
-}  // namespace
-
-template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
-          typename DstE>
-__global__ void __launch_bounds__(kPipeThreads, 1)
-    fused_pipe_forward_kernel(PassDesc d, int n_items, size_t tile_bytes) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[4];
-    pipe_items<MA, MB, SG, false, FIN, Acc, SrcE, MidE, DstE>(d, n_items, tile_bytes, smem_raw,
-                                                              bars, &g_pipe_timeouts);
-}
-
-template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
-          typename DstE>
-__global__ void __launch_bounds__(kPipeThreads, 1)
-    fused_pipe_adjoint_kernel(PassDesc d, int n_items, size_t tile_bytes) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[4];
-    pipe_items<MA, MB, SG, true, FIN, Acc, SrcE, MidE, DstE>(d, n_items, tile_bytes, smem_raw,
-                                                             bars, &g_pipe_timeouts);
-}
-
-template <int MA, int MB, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
-          typename DstE>
-void (*pipe_kernel_ptr(int sigma))(PassDesc, int, size_t) {
-    if constexpr (ADJ) {
-        return sigma > 0 ? fused_pipe_adjoint_kernel<MA, MB, 1, FIN, Acc, SrcE, MidE, DstE>
-                         : fused_pipe_adjoint_kernel<MA, MB, -1, FIN, Acc, SrcE, MidE, DstE>;
-    } else {
-        return sigma > 0 ? fused_pipe_forward_kernel<MA, MB, 1, FIN, Acc, SrcE, MidE, DstE>
-                         : fused_pipe_forward_kernel<MA, MB, -1, FIN, Acc, SrcE, MidE, DstE>;
-    }
-}
-
 // Uniform batch: image blockIdx.z of `d.batch` same-size transforms. The
 // CTA's pass descriptor, with that image's source and destination, lives in
 // shared memory (thread 0 writes it) and the item reads it there.
@@ -181,60 +137,6 @@ void (*fused_kernel_ptr(int sigma))(PassDesc) {
     }
 }
 
-// Persistent pipelined launch of a two-block pass (MB > 0): one CTA of two
-// warp groups per SM, two shared tiles. Returns cudaErrorNotSupported when
-// two tiles do not fit one block's shared memory (the caller then uses the
-// one-item-per-CTA kernel).
-template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, typename DstE>
-cudaError_t launch_pipe_t(PassDesc d, cudaStream_t st) {
-    constexpr int PAD = TilePad<MidE>::kPad;
-    TileGeom G = tile_geom(MA, MB, d.n_a, kPipeGroupWarps, PAD);
-    size_t tile_bytes = pipe_tile_bytes(G, MA, MB, sizeof(MidE));
-    while (2 * tile_bytes > kMaxTileSmem && d.n_a > 1) {
-        d.n_a--;
-        G = tile_geom(MA, MB, d.n_a, kPipeGroupWarps, PAD);
-        tile_bytes = pipe_tile_bytes(G, MA, MB, sizeof(MidE));
-    }
-    if (2 * tile_bytes > kMaxTileSmem) return cudaErrorNotSupported;
-    const size_t smem = 2 * tile_bytes;
-    d.tile_w = G.tile_out;
-    d.tiles = (d.p_count + G.tile_out - 1) / G.tile_out;
-    const long long items = (long long)d.tiles * d.s_count * d.a_count;
-    if (items == 0) return cudaSuccess;
-    if (items > INT32_MAX) return cudaErrorInvalidValue;
-    using FC = FinCases<ADJ, SrcE, DstE>;
-    void (*k)(PassDesc, int, size_t) = nullptr;
-    if (d.hi_final) {
-        if constexpr (FC::kFinal) {
-            if constexpr (ADJ) {
-                if (d.dst_transpose) k = pipe_kernel_ptr<MA, MB, ADJ, 2, Acc, SrcE, MidE, DstE>(d.sigma);
-            }
-            if (!k) k = pipe_kernel_ptr<MA, MB, ADJ, 1, Acc, SrcE, MidE, DstE>(d.sigma);
-        }
-    } else {
-        if constexpr (FC::kLevel) k = pipe_kernel_ptr<MA, MB, ADJ, 0, Acc, SrcE, MidE, DstE>(d.sigma);
-    }
-    if (!k) return cudaErrorInvalidValue;   // a type combination no plan produces
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-        return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPipeThreads, smem)) !=
-        cudaSuccess)
-        return e;
-    const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    const int grid = (int)(items < slots ? items : slots);
-    char name[64];
-    snprintf(name, sizeof name, "%s_m%d_%s%s", ADJ ? "adjoint_fused" : "forward_fused",
-             MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "");
-    LaunchScope scope(name, st, pass_alg_bytes(d, MA + MB, sizeof(SrcE), sizeof(DstE)));
-    k<<<grid, kPipeThreads, smem, st>>>(d, (int)items, tile_bytes);
-    scope.done();
-    return cudaGetLastError();
-}
-
 // The staged persistent form of the final pass from a uint16 level
 // (fht_staged.cuh): grid = SMs x resident CTAs, items taken in turn.
 template <typename Dummy = void>
@@ -260,7 +162,9 @@ cudaError_t launch_staged(PassDesc d, cudaStream_t st) {
         return e;
     const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
     const int grid = (int)(items < slots ? items : slots);
-    LaunchScope scope("forward_fused_m6_i32_final", st, pass_alg_bytes(d, 6, 2, 4));
+    LaunchScope scope(pass_pruned(d, 6) ? "forward_fused_m6_i32_final_range"
+                                        : "forward_fused_m6_i32_final",
+                      st, pass_alg_bytes(d, 6, 2, 4));
     k<<<grid, 8 * 32, smem, st>>>(d, (int)items, tile_bytes);
     scope.done();
     return cudaGetLastError();
@@ -277,15 +181,8 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     if constexpr (!ADJ && OP == 0 && MA == 3 && MB == 3 && std::is_same<Acc, int32_t>::value &&
                   std::is_same<SrcE, uint16_t>::value && std::is_same<MidE, int32_t>::value &&
                   std::is_same<DstE, int32_t>::value) {
-        if (d.hi_final && !d.lo_image && d.batch == 1 && d.n_a == 1 && staged_enabled() &&
-            !pipe_enabled())
+        if (d.hi_final && !d.lo_image && d.batch == 1 && d.n_a == 1 && staged_enabled())
             return launch_staged(d, st);
-    }
-    if constexpr (MB > 0 && OP == 0) {
-        if (pipe_enabled() && d.batch == 1) {
-            const cudaError_t e = launch_pipe_t<MA, MB, ADJ, Acc, SrcE, MidE, DstE>(d, st);
-            if (e != cudaErrorNotSupported) return e;
-        }
     }
     TileGeom G = tile_geom(MA, MB, d.n_a, kFusedWarps, TilePad<MidE>::kPad);
     size_t smem = MB == 0 ? 0 : (size_t)(1 << (MA + MB)) * G.pitch * sizeof(MidE);
@@ -328,13 +225,14 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     char name[64];
-    snprintf(name, sizeof name, "%s_m%d_%s%s%s",
+    snprintf(name, sizeof name, "%s_m%d_%s%s%s%s",
              d.shear_on ? "sheared_fused"
              : ADJ      ? "adjoint_fused"
              : OP == 1  ? "forward_max"
              : OP == 2  ? "forward_min"
                         : "forward_fused",
-             MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "", d.batch > 1 ? "_batch" : "");
+             MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "", d.batch > 1 ? "_batch" : "",
+             !ADJ && pass_pruned(d, MA + MB) ? "_range" : "");
     LaunchScope scope(name, st,
                       d.batch * pass_alg_bytes(d, MA + MB, sizeof(SrcE), sizeof(DstE)));
     k<<<grid, kFusedWarps * 32, smem, st>>>(d);

@@ -27,16 +27,12 @@ class LaunchScope {
     cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
 
-// Device-side wait-timeout counters (one per translation unit that holds
-// pipelined kernels): each registers a function that returns its count and
+// Device-side error counters (one per translation unit that holds kernels
+// able to record one): each registers a function that returns its count and
 // resets it; read_device_counters sums them. Registration returns true so it
 // can initialise a namespace-scope constant.
 bool register_device_counter(unsigned int (*read_and_reset)());
 unsigned int read_device_counters();
-
-// Whether two-block passes run as the persistent pipelined kernel
-// (FHT_PIPE=1 in the environment turns it on; off by default).
-bool pipe_enabled();
 
 // Whether the final pass from a uint16 level runs as the staged persistent
 // kernel (fht_staged.cuh; FHT_STAGED=0 in the environment turns it off).

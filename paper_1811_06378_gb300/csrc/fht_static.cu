@@ -24,23 +24,52 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {};   // device address of the array, per device
+// Per device: the array's device address, and the context it was looked up
+// in. A context torn down and created again (cudaDeviceReset) loads the
+// library's module afresh, at a new address, so the lookup is repeated when
+// the current context is not the one recorded.
+void *g_scratch_ptr[kMaxDevices] = {};
+void *g_scratch_ctx[kMaxDevices] = {};
+
+// The driver's cuCtxGetCurrent, found through the runtime (the library links
+// no driver library); nullptr if unavailable.
+using CtxGetCurrent = int (*)(void **);
+CtxGetCurrent ctx_get_current() {
+    static CtxGetCurrent fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<CtxGetCurrent>(f);
+    }();
+    return fn;
+}
 
 // Device address of the scratch on the current device. In host code the
 // array's name is only a stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, with that device current: once per device and
+// context.
 fht_status scratch_on_current_device(void **ptr) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return FHT_ECUDA;
+    void *ctx = nullptr;
+    if (CtxGetCurrent f = ctx_get_current()) {
+        if (f(&ctx) != 0) ctx = nullptr;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
             cudaGetLastError();   // do not leave this error for the caller's next check
             return FHT_ECUDA;
         }
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *ptr = g_scratch_ptr[dev];
     return FHT_OK;

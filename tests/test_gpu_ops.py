@@ -60,7 +60,8 @@ def test_sum_through_forward_op_is_forward_range(fht):
     img = edges_and_lines(257, 300, seed=3)
     x = dev(img)
     for q in range(4):
-        assert torch.equal(fht.forward_op(x, q, 0, 5, 90), fht.forward_range(x, q, 5, 90))
+        got = fht.forward_op(x, q, 0, 5, 90).cpu().numpy().astype(np.int64)
+        assert (got == O.range_slice(img, q, 5, 90)).all(), q
 
 
 def test_max_of_edge_map_marks_the_sum_support(fht):
@@ -68,6 +69,5 @@ def test_max_of_edge_map_marks_the_sum_support(fht):
     sum is positive (4096 x 4096, the benchmark's image)."""
     img = edges_and_lines(4096, 4096, p_edge=0.05, n_lines=4, seed=4096)
     x = dev(img)
-    mx = fht.forward_op(x, 0, 1)
-    s = fht.forward(x, 0)
-    assert torch.equal(mx, (s > 0).to(torch.int32))
+    mx = fht.forward_op(x, 0, 1).cpu().numpy()
+    assert (mx == (O.quadrant(img, 0) > 0)).all()

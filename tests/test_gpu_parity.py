@@ -230,8 +230,10 @@ def test_autograd_matches_adjoint_and_descends(fht):
     y = fht.FHTFunction.apply(x)
     loss = ((y - b) ** 2).sum()
     loss.backward()
-    expect = 2.0 * fht.adjoint((y - b).detach(), h, w)
-    assert torch.equal(x.grad, expect)
+    # d loss / d y = 2 (y - b), and scaling by 2 commutes with every FP32 add
+    r = (y - b).detach().cpu().numpy()
+    expect = 2.0 * O.adjoint_full(r, h, w, "f32")
+    assert np.array_equal(x.grad.cpu().numpy(), expect)
     # finite difference of the loss along one coordinate (float64 on the host)
     xh = np.zeros((h, w))
     bh = O.full(xt.astype(np.float64), "f64")
@@ -379,17 +381,18 @@ def test_config_batch_shapes_per_image(fht):
 def test_range_pruning_matches_full_rows(fht, h, w, q):
     """forward_range skips butterfly items whose slopes no later pass uses;
     ranges that start and end inside items, groups and passes (two-pass
-    K = 11, three-pass K = 13) give exactly the rows of the full quadrant,
-    itself checked against the oracle by the other tests."""
-    x = dev(edges_and_lines(h, w, seed=h + w + q))
-    full = fht.forward(x, q)
+    K = 11, three-pass K = 13) give exactly the rows of the oracle's full
+    quadrant."""
+    img = edges_and_lines(h, w, seed=h + w + q)
+    x = dev(img)
+    full = O.quadrant(img, q)
     n = full.shape[0]
     rng = np.random.default_rng(q)
     cases = [(0, 0), (n - 1, n - 1), (5, 9), (63, 64), (100, 131), (n // 2 - 3, n // 2 + 70)]
     cases += [tuple(sorted(rng.integers(0, n, size=2))) for _ in range(4)]
     for t_lo, t_hi in cases:
-        got = fht.forward_range(x, q, int(t_lo), int(t_hi))
-        assert torch.equal(got, full[t_lo:t_hi + 1]), (t_lo, t_hi)
+        got = host(fht.forward_range(x, q, int(t_lo), int(t_hi)))
+        assert (got == full[t_lo:t_hi + 1]).all(), (t_lo, t_hi)
 
 
 
@@ -451,7 +454,7 @@ def test_max_size_32768_sampled(fht, h, w, q, kind):
     del H
     torch.cuda.empty_cache()
 
-def test_zz_no_pipelined_wait_timed_out(fht):
-    """Every pipelined pass run by this module finished all its hand-offs
-    (runs last in the module: the count covers all the launches above)."""
+def test_zz_no_device_error_recorded(fht):
+    """No kernel run by this module recorded a device-side error (runs last
+    in the module: the count covers all the launches above)."""
     assert fht.device_status() == fht.FHT_OK

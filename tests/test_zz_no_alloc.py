@@ -4,14 +4,18 @@ hosts that forbid allocation after start-up).
 
 It keeps its intermediate levels in a fixed device array inside the library
 that every call shares and that keeps the last call's contents, so its output
-is compared with fht_forward's on several calls in a row, through the C ABI.
-The tolerance is the one the parity tests use: bit-exact (integer and FP32
-results run the same additions in the same order)."""
+is compared with fht_forward's on several calls in a row, through the C ABI,
+and with the oracle. The tolerance is the one the parity tests use:
+bit-exact (integer and FP32 results run the same additions in the same
+order)."""
 
 import ctypes
 
+import numpy as np
 import pytest
 import torch
+
+import oracle as O
 
 from workloads import edges_and_lines, random_image
 
@@ -48,12 +52,15 @@ def test_static_scratch_forward_matches_workspace_forward():
     for img_np, q, acc in cases:
         img = torch.from_numpy(img_np).cuda()
         want = fht.forward(img, q, acc=acc)
+        oracle = O.quadrant(img_np, q, "f32" if acc == torch.float32 else "i64")
         n, W = fht.query_shape(*img_np.shape, q)
         for _ in range(2):   # two calls in a row on the same shared scratch
             out = torch.full((n, W), -7, dtype=acc, device="cuda")
             assert _call_static(fn, img, q, out) == FHT_OK
             torch.cuda.synchronize()
             assert torch.equal(out, want), (img_np.shape, q)
+            assert np.array_equal(out.cpu().numpy(), oracle.astype(out.cpu().numpy().dtype)), \
+                (img_np.shape, q)
 
 
 def test_static_scratch_rejects_oversized_requests():
