@@ -680,6 +680,7 @@ def run_ours(args):
                    "launches_per_step": launches_per_step,
                    "tuning": {"levels_per_pass_tile_u8_tile_wide":
                               list(fht.get_tuning(int(math.log2(fht.query_shape(S, S, 0)[0])))),
+                              "batched": fht.get_batched_tuning(),
                               "table": os.environ.get("FHT_TUNE_FILE",
                                                       os.path.basename(fht.TUNING_FILE)
                                                       if os.path.exists(fht.TUNING_FILE)
@@ -846,6 +847,21 @@ def run_ours(args):
             lambda: fht.forward_sheared(img, sq, spl, st0, st1, out=sh_out, workspace=sh_ws),
             S * S + sh_out.numel() * 4, S * S)
         del sh_out, sh_ws
+        # Section 4, both operations: the [-15, 15] degree range as ONE scaled
+        # and sheared quadrant (alpha = 1/(2 tan 15 deg), spl = 1/2): every slope
+        # row inside the range, angles resolved 1.87 times finer
+        cq, ca, cs, c0, c1 = fht.scale_range(*RANGE_DEG, S, S)
+        sc_out = torch.empty((c1 - c0 + 1, fht.scaled_shape(S, S, cq, ca)[1]),
+                             dtype=torch.int32, device=dev)
+        sc_ws = torch.empty(max(fht.workspace_size_scaled(S, S, cq, ca, torch.uint8,
+                                                          torch.int32), 1),
+                            dtype=torch.uint8, device=dev)
+        rows["scaled_range_pm15deg_int32"] = row_entry(
+            lambda: fht.forward_scaled(img, cq, ca, cs, c0, c1, out=sc_out, workspace=sc_ws),
+            S * S + sc_out.numel() * 4, S * S)
+        rows["scaled_range_pm15deg_int32"].update(
+            {"alpha": ca, "spl": cs, "rows": c1 - c0 + 1, "cols": sc_out.shape[1]})
+        del sc_out, sc_ws
         # other operations: the maximum along every pattern of Q0
         rows["max_q0_int32"] = row_entry(
             lambda: fht.forward_op(img, 0, fht.OP_MAX, out=H0, workspace=ws_adj),

@@ -300,6 +300,62 @@ fht_status fht_forward_sheared(const void *img, fht_dtype in_t, int h, int w, in
 fht_status fht_shear_range(double phi_lo, double phi_hi, int h, int w, fht_quadrant *q,
                            double *spl, int *t_lo, int *t_hi);
 
+/* ------------------------------------------------------------ scaled (Section 4)
+ * The paper's other operation for a chosen range of angles: the image scaled
+ * along its rows by alpha > 0 (for Q2/Q3 the rows of the transposed image,
+ * i.e. the original scaled along OY) inside the first butterfly iteration; a
+ * line with dx/dy = k becomes one with dx/dy = alpha*k. The paper fixes no
+ * discrete resampling; this library takes nearest neighbour on the integer
+ * grid, in fixed point so that it is exact and reproducible: with
+ * D = ceil(2^32 / alpha) (the quotient in double), column c of the scaled row
+ * is image column (c * D) >> 32 (floor(c / k) for an integer factor k: every
+ * column repeated k times; k*c for alpha = 1/k), for the
+ * w_alpha = ceil(w * 2^32 / D) columns whose source lies in the row. The
+ * shear of fht_forward_sheared then applies to the scaled rows (scale first,
+ * then shear), on the cyclic width W = w_alpha + n:
+ *   Hs[t][x] = sum_{y<n} S[y][(x + sigma*off_n(t,y) - s(y)) mod W],
+ * S the scaled image zero-padded to W columns. A line with dx/dy = k lies on
+ * slope alpha*k + spl. Every intermediate level is all W columns wide. */
+
+/* Scaled width w_alpha of a row of w pixels (HOST). FHT_EINVAL unless
+ * 1/256 <= alpha <= 256 and 1 <= w_alpha <= 32768. */
+fht_status fht_scaled_width(int w, double alpha, int *w_alpha);
+
+/* Shape (rows n, cols W = w_alpha + n) of the scaled quadrant q of an h x w
+ * image; w_alpha scales w for Q0/Q1 and h for Q2/Q3. */
+fht_status fht_scaled_shape(int h, int w, fht_quadrant q, double alpha, int *rows, int *cols);
+
+/* Workspace bytes of fht_forward_scaled for this size, quadrant, factor and
+ * types. */
+fht_status fht_workspace_size_scaled(int h, int w, fht_quadrant q, double alpha,
+                                     fht_dtype in_t, fht_dtype acc_t, size_t *bytes);
+
+/* Slope rows t_lo..t_hi of quadrant q of the image scaled by alpha and then
+ * sheared by spl (-1 <= spl <= 1; spl = 0: no shear) into out
+ * ((t_hi - t_lo + 1) x W, pitch out_pitch >= W, row t at out row t - t_lo);
+ * W from fht_scaled_shape; types as fht_forward. Only the slopes those rows
+ * depend on are computed. alpha = 1 gives exactly fht_forward_sheared.
+ * FHT_EINVAL for factors or sizes fht_scaled_shape rejects. */
+fht_status fht_forward_scaled(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                              fht_quadrant q, double alpha, double spl, int t_lo, int t_hi,
+                              void *out, fht_dtype acc_t, int64_t out_pitch, void *workspace,
+                              size_t workspace_bytes, void *stream);
+
+/* One scaled and sheared quadrant for the line angles [phi_lo, phi_hi]
+ * (degrees), host only: the two operations map the range onto as many slope
+ * rows as |spl| <= 1 allows, resolving its angles alpha times finer than the
+ * plain quadrant. A mostly vertical range (midpoint in [-45, 45], ends inside
+ * (-90, 90)) gives Q0 with alpha = min(1/(tan b - tan a), 1/|tan b|, 16),
+ * spl = alpha*tan b, and row t holding atan((spl - t/(n-1))/alpha) (phi_hi
+ * at t = 0), a = phi_lo, b = phi_hi. A mostly horizontal one (midpoint in
+ * (45, 135], ends inside (0, 180)) gives Q3 with a, b measured from 90
+ * degrees, alpha = min(1/(tan b - tan a), 1/|tan a|, 16), spl = -alpha*tan a,
+ * and row t holding 90 + atan((t/(n-1) - spl)/alpha) (phi_lo at t = 0).
+ * t_lo = 0, t_hi = floor((n-1) * alpha * (tan b - tan a)). FHT_EINVAL
+ * otherwise. */
+fht_status fht_scale_range(double phi_lo, double phi_hi, int h, int w, fht_quadrant *q,
+                           double *alpha, double *spl, int *t_lo, int *t_hi);
+
 /* ------------------------------------------------------------ uniform batches
  * `batch` transforms of the same size and layout in one launch per pass (the
  * launch's third grid dimension is the image), so that many small images fill
@@ -357,6 +413,34 @@ typedef struct {
 fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_quadrant q,
                                    fht_dtype in_t, fht_dtype acc_t, fht_plan **plan,
                                    size_t *workspace_bytes);
+
+/* How batched plans cut their work (not in the paper; every setting gives the
+ * same results bit for bit). Read when a plan is created; the package's
+ * autotuner times the candidates on a batch and sets the fastest. */
+typedef struct {
+    int units_per_item;   /* (group, tile) units one claimed work item covers:
+                             the per-item bookkeeping is paid once for them;
+                             1..16 (default 4) */
+    int tile_u8;          /* warp-widths (248 columns) of block-A source columns
+                             in first passes over uint8 images: 1..3 (default 2) */
+    int tile_wide;        /* the same for passes with 4-byte shared tiles: 1..3
+                             (default 1, widened to one block-A item per warp) */
+    int ctas_per_sm;      /* CTAs of the persistent kernel per SM, i.e. its
+                             register budget: 2 (128 registers) or 3 (80);
+                             default 2 */
+    int first_levels[13]; /* index K (7..12): butterfly levels of the first of
+                             the two passes of an image with 2^K padded rows
+                             ("stages per CTA"), K-6..6; 0 = the default
+                             ceil(K/2). Entries below 7 are ignored (images
+                             up to 64 rows take one pass). */
+} fht_batched_tuning;
+
+/* Use `t` for batched plans created from now on, process-wide; NULL restores
+ * the defaults. FHT_EINVAL for values out of range (nothing changes). */
+fht_status fht_set_batched_tuning(const fht_batched_tuning *t);
+
+/* The batched tuning in use (HOST struct). */
+fht_status fht_get_batched_tuning(fht_batched_tuning *out);
 
 /* Transform the batch: descs is a HOST array of `count` descriptors, checked
  * against the plan; workspace is >= workspace_bytes, 256-byte aligned. One

@@ -21,6 +21,8 @@ What is computed (Aliev, Ershov, Nikolaev, arXiv:1811.06378):
 * ``point_segment`` the image pixels one Hough point sums (Section 3.2).
 * ``quadrant_op``  maximum or minimum along the patterns instead of the sum.
 * ``sheared_quadrant`` the quadrant of the sheared image (Section 4).
+* ``scaled_quadrant`` the quadrant of the image scaled along its rows, then
+                   sheared (Section 4, both operations).
 * ``adjoint_*``    the transpose of each map (not in the paper; defined by the
                    transform being linear), computed as the opposite-sign
                    transform of the gradient because the dyadic offsets are
@@ -46,6 +48,13 @@ with gcc, no fast-math). Readings of points the paper leaves open:
    quadrant transform runs on the cyclic width W = w + n, which the paper
    keeps (Section 4: the black zone only moves, nothing wraps into the
    meaningful zone).
+9. The scale of Section 4 (``scaled_quadrant``): the paper fixes no discrete
+   resampling. Column x' of the row scaled by alpha is column
+   floor(x' * D / 2^32) of the original, D = ceil(2^32 / alpha) (nearest
+   neighbour on the integer grid, in fixed point so that both sides take the
+   same integer decision), for the w_alpha = ceil(w * 2^32 / D) columns whose
+   source lies inside the row. The scale comes first, then the shear, on the
+   cyclic width w_alpha + n.
 """
 
 from __future__ import annotations
@@ -461,6 +470,98 @@ def shear_range(phi_lo: float, phi_hi: float, h: int, w: int
     n, _ = quadrant_geometry(h, w, q)
     t_hi = 0 if n == 1 else min(n - 1, math.floor((n - 1) * span + 1e-9))
     return q, spl, 0, t_hi
+
+
+# ---------------------------------------------------------------- scale (Section 4)
+
+def scale_step(alpha: float) -> int:
+    """Source-column step of the image scaled along OX by alpha, in fixed
+    point with 32 fractional bits, rounded up: D = ceil(2^32 / alpha), the
+    quotient taken in float64 (the library computes the same double)."""
+    return int(math.ceil(2.0**32 / float(alpha)))
+
+
+def scaled_width(w: int, alpha: float) -> int:
+    """Columns x' of the scaled row whose source column src(x') = floor(x' *
+    D / 2^32) lies inside the w image columns: ceil(w * 2^32 / D)."""
+    D = scale_step(alpha)
+    return (w * 2**32 + D - 1) // D
+
+
+def scale_columns(w: int, alpha: float) -> np.ndarray:
+    """src(x') = floor(x' * D / 2^32) for every column x' of the scaled row:
+    nearest-neighbour resampling on the integer grid (the paper fixes no
+    rule); exactly floor(x'/k) for an integer factor k (each column repeated
+    k times) and k*x' for alpha = 1/k (every k-th column)."""
+    D = scale_step(alpha)
+    return np.array([(x * D) >> 32 for x in range(scaled_width(w, alpha))], dtype=np.int64)
+
+
+def scaled_image(img: np.ndarray, alpha: float) -> np.ndarray:
+    """The image scaled along OX by alpha > 0 (Section 4, first operation):
+    column x' of the result is column src(x') of img. A line with dx/dy = k
+    becomes one with dx/dy = alpha * k, the paper's tg(beta) -> alpha*tg(beta)."""
+    return img[:, scale_columns(img.shape[1], alpha)]
+
+
+def scaled_quadrant(img: np.ndarray, q: int, alpha: float, spl: float = 0.0,
+                    kind: str = "i64", t_lo: int = 0, t_hi: int | None = None) -> np.ndarray:
+    """Quadrant q after both operations of Section 4: the image (the
+    transposed image for Q2/Q3, i.e. the original scaled along OY) scaled
+    along its rows by alpha, then sheared by spl; the butterfly of that n x W
+    array with W = w_alpha + n (w_alpha = scaled_width of the row length) and
+    the quadrant's sign, rows t_lo..t_hi. A line with dx/dy = k (columns per
+    row of the transposed image for Q2/Q3) lies on slope alpha*k + spl."""
+    src = img.T if TRANSPOSED[q] else img
+    scaled = scaled_image(src, alpha)
+    n = next_pow2(src.shape[0])
+    W = scaled.shape[1] + n
+    P = padded(scaled, n, W, kind)
+    s = shear_shifts(src.shape[0], spl)
+    for y in range(src.shape[0]):
+        P[y] = np.roll(P[y], int(s[y]))
+    H = butterfly(P, SIGMA[q], kind)
+    t_hi = n - 1 if t_hi is None else t_hi
+    return H[t_lo:t_hi + 1].copy()
+
+
+def scale_range(phi_lo: float, phi_hi: float, h: int, w: int, alpha_max: float = 16.0):
+    """One scaled and sheared quadrant for the line angles [phi_lo, phi_hi]
+    (degrees, the quadrant spans of ``angle_to_slopes``): (q, alpha, spl,
+    t_lo, t_hi), or None. The two operations of Section 4 map the range onto
+    as many of the quadrant's slope rows as the shear's |spl| <= 1 allows,
+    so that its angles are resolved alpha times finer than in the plain
+    quadrant.
+
+    Mostly vertical ranges (midpoint within [-45, 45], ends inside (-90, 90))
+    use Q0: row t holds phi(t) = atan((spl - t/(n-1)) / alpha), phi_hi at
+    t = 0, with alpha = min(1/(tan(b) - tan(a)), 1/|tan(b)|, alpha_max) and
+    spl = alpha*tan(b). Mostly horizontal ranges (midpoint within [45, 135],
+    ends inside (0, 180)) use Q3 with the angles a, b measured from 90
+    degrees: row t holds 90 + atan((t/(n-1) - spl) / alpha), phi_lo at t = 0,
+    alpha = min(1/(tan(b) - tan(a)), 1/|tan(a)|, alpha_max), spl =
+    -alpha*tan(a). t runs from 0 to floor((n-1) * alpha * (tan(b) - tan(a)))."""
+    if not phi_lo <= phi_hi:
+        return None
+    mid = 0.5 * (phi_lo + phi_hi)
+    if -45.0 <= mid <= 45.0 and -90.0 < phi_lo and phi_hi < 90.0:
+        q, a, b = Q0, phi_lo, phi_hi
+        edge = math.tan(math.radians(b))
+    elif 45.0 < mid <= 135.0 and 0.0 < phi_lo and phi_hi < 180.0:
+        q, a, b = Q3, phi_lo - 90.0, phi_hi - 90.0
+        edge = math.tan(math.radians(a))
+    else:
+        return None
+    span = math.tan(math.radians(b)) - math.tan(math.radians(a))
+    alpha = alpha_max
+    if span > 0:
+        alpha = min(alpha, 1.0 / span)
+    if edge != 0:
+        alpha = min(alpha, 1.0 / abs(edge))
+    spl = alpha * edge if q == Q0 else -alpha * edge
+    n, _ = quadrant_geometry(h, w, q)
+    t_hi = 0 if n == 1 else min(n - 1, math.floor((n - 1) * alpha * span + 1e-9))
+    return q, alpha, spl, 0, t_hi
 
 
 # ---------------------------------------------------------------- adjoints

@@ -27,6 +27,8 @@ __all__ = [
     "workspace_size", "forward", "forward_range", "full_quadrants", "fhtshift",
     "adjoint", "FHTFunction", "profile_begin", "profile_end", "launch_count", "device_status",
     "workspace_size_many", "forward_many", "adjoint_many",
+    "workspace_size_sheared", "shear_range", "forward_sheared",
+    "scaled_width", "scaled_shape", "workspace_size_scaled", "scale_range", "forward_scaled",
     "BatchPlan", "FHT_OK", "FHT_ETIMEOUT",
 ]
 
@@ -48,6 +50,13 @@ class Tuning(ctypes.Structure):
     """fht_tuning: levels fused per pass and tile widths for 2^K-row quadrants."""
     _fields_ = [("max_levels", ctypes.c_int), ("tile_u8", ctypes.c_int),
                 ("tile_wide", ctypes.c_int)]
+
+
+class BatchedTuning(ctypes.Structure):
+    """fht_batched_tuning: how batched plans cut their work."""
+    _fields_ = [("units_per_item", ctypes.c_int), ("tile_u8", ctypes.c_int),
+                ("tile_wide", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("first_levels", ctypes.c_int * 13)]
 
 
 def _load() -> ctypes.CDLL:
@@ -78,6 +87,11 @@ def _load() -> ctypes.CDLL:
         "fht_row_argmax": (i, [vp, i, i, i, i64, vp, vp, vp]),
         "fht_forward_sheared": (i, [vp, i, i, i, i64, i, d, i, i, vp, i, i64, vp, sz, vp]),
         "fht_shear_range": (i, [d, d, i, i, ip, ctypes.POINTER(d), ip, ip]),
+        "fht_scaled_width": (i, [i, d, ip]),
+        "fht_scaled_shape": (i, [i, i, i, d, ip, ip]),
+        "fht_workspace_size_scaled": (i, [i, i, i, d, i, i, ctypes.POINTER(sz)]),
+        "fht_forward_scaled": (i, [vp, i, i, i, i64, i, d, d, i, i, vp, i, i64, vp, sz, vp]),
+        "fht_scale_range": (i, [d, d, i, i, ip, ctypes.POINTER(d), ctypes.POINTER(d), ip, ip]),
         "fht_plan_create_batched": (i, [ctypes.POINTER(i), ctypes.POINTER(i), i, i, i, i,
                                         ctypes.POINTER(vp), ctypes.POINTER(sz)]),
         "fht_forward_batched": (i, [vp, vp, vp, sz, vp]),
@@ -95,6 +109,8 @@ def _load() -> ctypes.CDLL:
     }
     sigs["fht_set_tuning"] = (i, [i, ctypes.POINTER(Tuning)])
     sigs["fht_get_tuning"] = (i, [i, ctypes.POINTER(Tuning)])
+    sigs["fht_set_batched_tuning"] = (i, [ctypes.POINTER(BatchedTuning)])
+    sigs["fht_get_batched_tuning"] = (i, [ctypes.POINTER(BatchedTuning)])
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
         fn.restype = res
@@ -152,6 +168,34 @@ def get_tuning(K: int) -> tuple[int, int, int]:
     return t.max_levels, t.tile_u8, t.tile_wide
 
 
+def set_batched_tuning(t: dict | None) -> None:
+    """Tuning of batched plans created from now on (fht_set_batched_tuning):
+    a dict with units_per_item, tile_u8, tile_wide, ctas_per_sm and
+    first_levels ({K: levels}); missing keys keep their current values; None
+    restores the defaults."""
+    if t is None:
+        _check(lib.fht_set_batched_tuning(None), "fht_set_batched_tuning")
+        return
+    cur = BatchedTuning()
+    _check(lib.fht_get_batched_tuning(ctypes.byref(cur)), "fht_get_batched_tuning")
+    for k in ("units_per_item", "tile_u8", "tile_wide", "ctas_per_sm"):
+        if k in t:
+            setattr(cur, k, int(t[k]))
+    for K, f in (t.get("first_levels") or {}).items():
+        cur.first_levels[int(K)] = int(f)
+    _check(lib.fht_set_batched_tuning(ctypes.byref(cur)), "fht_set_batched_tuning")
+
+
+def get_batched_tuning() -> dict:
+    """The batched tuning in use, as set_batched_tuning takes it."""
+    t = BatchedTuning()
+    _check(lib.fht_get_batched_tuning(ctypes.byref(t)), "fht_get_batched_tuning")
+    return {"units_per_item": t.units_per_item, "tile_u8": t.tile_u8,
+            "tile_wide": t.tile_wide, "ctas_per_sm": t.ctas_per_sm,
+            "first_levels": {K: t.first_levels[K] for K in range(7, 13)
+                             if t.first_levels[K]}}
+
+
 TUNING_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 
 
@@ -161,6 +205,8 @@ def load_tuning(path: str) -> dict:
         res = json.load(f)
     for k, e in res["table"].items():
         set_tuning(int(k), int(e["max_levels"]), int(e["tile_u8"]), int(e["tile_wide"]))
+    if "batched" in res:
+        set_batched_tuning(res["batched"]["tuning"])
     return res
 
 
@@ -421,6 +467,67 @@ def forward_sheared(img: torch.Tensor, q: int, spl: float, t_lo: int = 0,
     _check(lib.fht_forward_sheared(_ptr(img), in_code, h, w, in_pitch, q, float(spl), t_lo,
                                    t_hi, _ptr(out), out_code, out_pitch, _ptr(ws), _nbytes(ws),
                                    _stream(stream)), "fht_forward_sheared")
+    return out
+
+
+# ------------------------------------------------------------------ scaled (Section 4)
+
+def scaled_width(w: int, alpha: float) -> int:
+    """Columns of a row of w pixels scaled by alpha (fht_scaled_width)."""
+    wa = ctypes.c_int()
+    _check(lib.fht_scaled_width(w, float(alpha), ctypes.byref(wa)), "fht_scaled_width")
+    return wa.value
+
+
+def scaled_shape(h: int, w: int, q: int, alpha: float) -> tuple[int, int]:
+    """(n, W) of the scaled quadrant q of an h x w image (fht_scaled_shape)."""
+    r, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib.fht_scaled_shape(h, w, q, float(alpha), ctypes.byref(r), ctypes.byref(c)),
+           "fht_scaled_shape")
+    return r.value, c.value
+
+
+def workspace_size_scaled(h: int, w: int, q: int, alpha: float, in_dtype: torch.dtype,
+                          acc: torch.dtype) -> int:
+    n = ctypes.c_size_t()
+    _check(lib.fht_workspace_size_scaled(h, w, q, float(alpha), _DTYPE[in_dtype], _DTYPE[acc],
+                                         ctypes.byref(n)), "fht_workspace_size_scaled")
+    return n.value
+
+
+def scale_range(phi_lo: float, phi_hi: float, h: int,
+                w: int) -> tuple[int, float, float, int, int]:
+    """(q, alpha, spl, t_lo, t_hi): the one scaled and sheared quadrant and
+    its slope rows for the line angles [phi_lo, phi_hi] degrees
+    (fht_scale_range)."""
+    q, t_lo, t_hi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    alpha, spl = ctypes.c_double(), ctypes.c_double()
+    _check(lib.fht_scale_range(phi_lo, phi_hi, h, w, ctypes.byref(q), ctypes.byref(alpha),
+                               ctypes.byref(spl), ctypes.byref(t_lo), ctypes.byref(t_hi)),
+           "fht_scale_range")
+    return q.value, alpha.value, spl.value, t_lo.value, t_hi.value
+
+
+def forward_scaled(img: torch.Tensor, q: int, alpha: float, spl: float = 0.0, t_lo: int = 0,
+                   t_hi: int | None = None, acc: torch.dtype = torch.int32,
+                   out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """Rows t_lo..t_hi of quadrant q of the image scaled along its rows by
+    alpha, then sheared by spl per row (Section 4; fht_forward_scaled)."""
+    in_code, in_pitch = _dev2d(img, "img")
+    h, w = img.shape
+    n, W = scaled_shape(h, w, q, alpha)
+    t_hi = n - 1 if t_hi is None else t_hi
+    if out is None:
+        out = torch.empty((t_hi - t_lo + 1, W), dtype=acc, device=img.device)
+    out_code, out_pitch = _dev2d(out, "out")
+    _shape(out, (t_hi - t_lo + 1, W), "out")
+    ws = _workspace(workspace, workspace_size_scaled(h, w, q, alpha, img.dtype, out.dtype),
+                    img.device)
+    _check(lib.fht_forward_scaled(_ptr(img), in_code, h, w, in_pitch, q, float(alpha),
+                                  float(spl), t_lo, t_hi, _ptr(out), out_code, out_pitch,
+                                  _ptr(ws), _nbytes(ws), _stream(stream)),
+           "fht_forward_scaled")
     return out
 
 

@@ -12,12 +12,23 @@ plain quadrant calls the library's workloads are made of, on seeded n x n
 inputs resident on the device: the uint8 -> int32 forward of Q0, the FP32
 forward of Q0 and the FP32 adjoint of Q0.
 
+The persistent batched kernel has its own plan (fht_batched_tuning): units
+of work per claimed item, tile widths, CTAs per SM (its register budget) and,
+per image size 2^K, how many of the K levels the first of its two passes
+fuses ("stages per CTA"). `tune_batched` searches it coordinate by
+coordinate on a batch of uint8 edge maps with sides log-uniform in
+[64, 1024] (the benchmark's batch), objective the sum of the median times of
+the batch's uint8 -> int32 forward and its FP32 adjoint, every candidate's
+results checked bit for bit against the default plan's.
+
 The result is a JSON table {"table": {K: {max_levels, tile_u8, tile_wide,
-us, default_us}}, ...}; `load` applies one to the library (fht_set_tuning),
+us, default_us}}, "batched": {"tuning": {...}, "us", "default_us"}, ...};
+`load` applies one to the library (fht_set_tuning, fht_set_batched_tuning),
 and the package loads its own table (tuning_gb300.json) when it is imported,
 or the one named by FHT_TUNE_FILE (FHT_TUNE_FILE=none loads nothing).
 
     python -m paper_1811_06378_gb300.autotune --out table.json --sizes 7-13
+    python -m paper_1811_06378_gb300.autotune --out table.json --batched
 """
 
 from __future__ import annotations
@@ -104,12 +115,92 @@ def tune(ks=range(7, 14), reps: int = 15, warmup: int = 3, device="cuda",
             "reps": reps, "table": table, "candidates": tried}
 
 
+def _batch_workload(count: int, seed: int, device):
+    """`count` uint8 edge maps (8% edges) with sides log-uniform in [64, 1024],
+    their FP32 quadrant gradients, and the calls that time them."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    shapes = [(int(h), int(w)) for h, w in
+              np.round(np.exp(rng.uniform(np.log(64), np.log(1024), size=(count, 2))))]
+    g = torch.Generator(device=device).manual_seed(seed)
+    imgs = [(torch.rand(sh, generator=g, device=device) < 0.08).to(torch.uint8) for sh in shapes]
+    grads = [torch.randn(fht.query_shape(h, w, fht.Q0), generator=g, device=device)
+             for h, w in shapes]
+    return shapes, imgs, grads
+
+
+def _time_batch(shapes, imgs, grads, reps, warmup, device):
+    """(us, outputs) of the batch's uint8 forward plus its FP32 adjoint
+    under the batched tuning in force."""
+    plan = fht.BatchPlan(shapes, fht.Q0)
+    ws = plan.workspace(device)
+    outs = [torch.empty(sh, dtype=torch.int32, device=device) for sh in plan.out_shapes]
+    fplan = fht.BatchPlan(shapes, fht.Q0, torch.float32, torch.float32)
+    fws = fplan.workspace(device)
+    gouts = [torch.empty(sh, dtype=torch.float32, device=device) for sh in shapes]
+    t = _median_us(lambda: plan.forward(imgs, outs, ws), reps, warmup)
+    t += _median_us(lambda: fplan.adjoint(grads, gouts, fws), reps, warmup)
+    if plan.status(ws) != 0 or fplan.status(fws) != 0:
+        raise RuntimeError("a batched wait ran out of its budget")
+    return t, outs, gouts
+
+
+def tune_batched(count: int = 512, seed: int = 3, reps: int = 10, warmup: int = 3,
+                 device="cuda", log=None) -> dict:
+    """Coordinate search of the batched plan; leaves the library set to the
+    best tuning found and returns the JSON-ready result."""
+    device = torch.device(device)
+    shapes, imgs, grads = _batch_workload(count, seed, device)
+    ks = sorted({max(0, (max(h, 1) - 1).bit_length()) for h, _ in shapes})
+    fht.set_batched_tuning(None)
+    best = fht.get_batched_tuning()
+    default_t, ref_o, ref_g = _time_batch(shapes, imgs, grads, reps, warmup, device)
+    best_t = default_t
+    if log:
+        log(f"batched default {best}: {default_t:.1f} us")
+    coords = [("ctas_per_sm", [2, 3]), ("units_per_item", [1, 2, 4, 8, 16]),
+              ("tile_u8", [1, 2, 3]), ("tile_wide", [1, 2, 3])]
+    coords += [(("first_levels", K), list(range(K - 6, 7))) for K in ks if 7 <= K <= 12]
+    tried = []
+    for key, values in coords:
+        for v in values:
+            cand = {**best, "first_levels": dict(best["first_levels"])}
+            if isinstance(key, tuple):
+                cand["first_levels"][key[1]] = v
+            else:
+                cand[key] = v
+            if cand == best:
+                continue
+            fht.set_batched_tuning(None)
+            fht.set_batched_tuning(cand)
+            t, o, g = _time_batch(shapes, imgs, grads, reps, warmup, device)
+            same = all(torch.equal(a, b) for a, b in zip(o, ref_o)) and \
+                all(torch.equal(a, b) for a, b in zip(g, ref_g))
+            if not same:
+                raise RuntimeError(f"batched tuning {cand} changed the results")
+            tried.append([json.dumps(cand, sort_keys=True), t])
+            if log:
+                log(f"batched {key}={v}: {t:.1f} us")
+            if t < best_t:
+                best_t, best = t, cand
+        torch.cuda.empty_cache()
+    fht.set_batched_tuning(None)
+    fht.set_batched_tuning(best)
+    return {"tuning": {**best, "first_levels": {str(k): v for k, v in best["first_levels"].items()}},
+            "us": best_t, "default_us": default_t, "images": count, "seed": seed,
+            "objective": "sum of median times (us) of the batch's uint8->int32 forward "
+                         "and FP32 adjoint (Q0), sides log-uniform in [64, 1024]",
+            "candidates": tried}
+
+
 def load(path_or_result) -> dict:
     """Apply a table (a JSON path or `tune`'s result) to the library."""
     if isinstance(path_or_result, (str, os.PathLike)):
         return fht.load_tuning(os.fspath(path_or_result))
     for k, e in path_or_result["table"].items():
         fht.set_tuning(int(k), int(e["max_levels"]), int(e["tile_u8"]), int(e["tile_wide"]))
+    if "batched" in path_or_result:
+        fht.set_batched_tuning(path_or_result["batched"]["tuning"])
     return path_or_result
 
 
@@ -123,7 +214,21 @@ def main():
     ap.add_argument("--out", required=True)
     ap.add_argument("--sizes", default="7-13", help="range of K (n = 2^K), e.g. 7-13")
     ap.add_argument("--reps", type=int, default=15)
+    ap.add_argument("--batched", action="store_true",
+                    help="tune the batched plan only and merge it into --out (kept "
+                         "per-size table, if the file exists)")
     args = ap.parse_args()
+    if args.batched:
+        res = {}
+        if os.path.exists(args.out):
+            with open(args.out) as f:
+                res = json.load(f)
+        res["batched"] = tune_batched(log=print)
+        with open(args.out, "w") as f:
+            json.dump(res, f, indent=1)
+        b = res["batched"]
+        print(f"batched: {b['tuning']}: {b['us']:.1f} us (default {b['default_us']:.1f} us)")
+        return
     for K in _parse_ks(args.sizes):   # time from the defaults, not a loaded table
         fht.set_tuning(K, None)
     res = tune(_parse_ks(args.sizes), reps=args.reps, log=print)

@@ -6,7 +6,9 @@
 namespace fht {
 namespace batched {
 
-Kernel kernel_adj_q0() { return batched_kernel<kModeAdj, -1>; }
+Kernel kernel_adj_q0(int minb) {
+    return minb >= 3 ? batched_kernel<kModeAdj, -1, 3> : batched_kernel<kModeAdj, -1, 2>;
+}
 
 }  // namespace batched
 }  // namespace fht

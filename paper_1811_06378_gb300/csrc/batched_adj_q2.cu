@@ -6,7 +6,9 @@
 namespace fht {
 namespace batched {
 
-Kernel kernel_adj_q2() { return batched_kernel<kModeAdjT, 1>; }
+Kernel kernel_adj_q2(int minb) {
+    return minb >= 3 ? batched_kernel<kModeAdjT, 1, 3> : batched_kernel<kModeAdjT, 1, 2>;
+}
 
 }  // namespace batched
 }  // namespace fht

@@ -5,7 +5,9 @@
 namespace fht {
 namespace batched {
 
-Kernel kernel_f32_pos() { return batched_kernel<kModeF32, 1>; }
+Kernel kernel_f32_pos(int minb) {
+    return minb >= 3 ? batched_kernel<kModeF32, 1, 3> : batched_kernel<kModeF32, 1, 2>;
+}
 
 }  // namespace batched
 }  // namespace fht

@@ -5,7 +5,9 @@
 namespace fht {
 namespace batched {
 
-Kernel kernel_u8_pos() { return batched_kernel<kModeU8, 1>; }
+Kernel kernel_u8_pos(int minb) {
+    return minb >= 3 ? batched_kernel<kModeU8, 1, 3> : batched_kernel<kModeU8, 1, 2>;
+}
 
 }  // namespace batched
 }  // namespace fht

@@ -144,9 +144,10 @@ struct QuadPlan {
 // symmetric in slope and row), every level all W columns wide and cyclic.
 // With `sheared`, the quadrant's own transform of the sheared image (Section
 // 4), also on cyclic full-width levels: the shear moves the black zone, so
-// the compact columns do not hold.
+// the compact columns do not hold. w_scaled > 0 replaces the content width
+// (columns of the (transposed) image) by that of its scaled rows (Section 4).
 QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
-                   bool adjoint = false, bool sheared = false, int op = 0) {
+                   bool adjoint = false, bool sheared = false, int op = 0, int w_scaled = 0) {
     QuadPlan P{};
     P.q = q;
     P.adjoint = adjoint;
@@ -158,6 +159,7 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
     if (adjoint) P.sigma = -P.sigma;
     P.h_c = P.transpose ? w : h;
     P.w_c = P.transpose ? h : w;
+    if (w_scaled > 0) P.w_c = w_scaled;
     P.n = next_pow2(P.h_c);
     P.K = ilog2(P.n);
     if (full) {
@@ -393,9 +395,10 @@ PassDesc pass_desc(const QuadPlan &P, int p, const Side &image, const Side &fina
 
 fht_status run_forward(const QuadPlan &P, const Side &image, const Side &out,
                        const FinalMap &fm, int t_lo, int t_hi, int acc_elem, void *ws,
-                       cudaStream_t st, const Batch &B = Batch{}) {
+                       cudaStream_t st, const Batch &B = Batch{}, bool range_call = false) {
     for (int p = 0; p < P.npass; ++p) {
         PassDesc d = pass_desc(P, p, image, out, ws, fm, t_lo, t_hi, B);
+        d.range_call = range_call ? 1 : 0;
         cudaError_t e = launch_forward(P.m[p], d, acc_elem, st);
         if (e != cudaSuccess) {
             g_last_cuda_error = (int)e;
@@ -766,7 +769,7 @@ static fht_status forward_common(const void *img, fht_dtype in_t, int h, int w,
     Side image{const_cast<void *>(img), in_pitch, elem_of(in_t), P.h_c, P.w_c};
     Side o{out, out_pitch, elem_of(acc_t), 0, P.W};
     return run_forward(P, image, o, quadrant_map(t_lo, t_hi), t_lo, t_hi, acc, ws,
-                       (cudaStream_t)stream);
+                       (cudaStream_t)stream, Batch{}, t_lo != 0 || t_hi != P.n - 1);
 }
 
 fht_status fht_forward(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
@@ -969,6 +972,7 @@ fht_status fht_forward_op(const void *img, fht_dtype in_t, int h, int w, int64_t
     Side o{out, out_pitch, elem_of(acc_t), 0, P.W};
     for (int p = 0; p < P.npass; ++p) {
         PassDesc d = pass_desc(P, p, image, o, workspace, quadrant_map(t_lo, t_hi), t_lo, t_hi);
+        d.range_call = t_lo != 0 || t_hi != P.n - 1;
         const cudaError_t e = launch_forward_op(P.m[p], d, acc, (int)op, (cudaStream_t)stream);
         if (e != cudaSuccess) {
             g_last_cuda_error = (int)e;
@@ -991,29 +995,22 @@ fht_status fht_workspace_size_sheared(int h, int w, fht_quadrant q, fht_dtype in
     return FHT_OK;
 }
 
-fht_status fht_forward_sheared(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
-                               fht_quadrant q, double spl, int t_lo, int t_hi, void *out,
-                               fht_dtype acc_t, int64_t out_pitch, void *workspace,
-                               size_t workspace_bytes, void *stream) {
-    if (!img || !out || !sizes_ok(h, w) || !quadrant_ok(q) || in_pitch < w || !spl_ok(spl))
-        return FHT_EINVAL;
-    const int acc = acc_kind(in_t, acc_t);
-    if (acc < 0) return FHT_EINVAL;
-    const int in_elem = elem_of(in_t);
-    QuadPlan P = make_plan(h, w, q, false, in_elem, acc, false, true);
-    if (P.K > kMaxK) return FHT_EINVAL;
-    if (t_lo < 0 || t_hi < t_lo || t_hi >= P.n || out_pitch < P.W) return FHT_EINVAL;
-    const size_t need = plan_workspace(P);
-    if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
+// The sheared (and optionally scaled) forward transform of Section 4 on the
+// cyclic pass code: every pass carries the shear in fixed point (shear_p) and
+// the scale step (0 = none); P was built with sheared = true (and the scaled
+// width).
+static fht_status run_sheared(const QuadPlan &P, const void *img, int in_elem, int64_t in_pitch,
+                              long long shear_p, long long scale_step, int t_lo, int t_hi,
+                              void *out, fht_dtype acc_t, int64_t out_pitch, void *workspace,
+                              cudaStream_t st) {
+    const int acc = P.acc_elem;
     Side image{const_cast<void *>(img), in_pitch, in_elem, P.h_c, P.w_c};
     Side o{out, out_pitch, elem_of(acc_t), 0, P.W};
-    cudaStream_t st = (cudaStream_t)stream;
     for (int p = 0; p < P.npass; ++p) {
         PassDesc d = pass_desc(P, p, image, o, workspace, quadrant_map(t_lo, t_hi), t_lo, t_hi);
         d.shear_on = 1;
-        // spl in fixed point, 32 fractional bits, rounded half up (exact in
-        // double for |spl| <= 1)
-        d.shear_p = (long long)std::floor(spl * 4294967296.0 + 0.5);
+        d.shear_p = shear_p;
+        d.scale_step = scale_step;
         if (d.hi_final) {
             // every column X of the slope rows [t_lo, t_hi]: p = X + sigma_plus * n
             d.dst_image = 1;
@@ -1044,6 +1041,131 @@ fht_status fht_forward_sheared(const void *img, fht_dtype in_t, int h, int w, in
             return FHT_ECUDA;
         }
     }
+    return FHT_OK;
+}
+
+// spl in fixed point, 32 fractional bits, rounded half up (exact in double
+// for |spl| <= 1)
+static long long shear_fixed(double spl) { return (long long)std::floor(spl * 4294967296.0 + 0.5); }
+
+fht_status fht_forward_sheared(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                               fht_quadrant q, double spl, int t_lo, int t_hi, void *out,
+                               fht_dtype acc_t, int64_t out_pitch, void *workspace,
+                               size_t workspace_bytes, void *stream) {
+    if (!img || !out || !sizes_ok(h, w) || !quadrant_ok(q) || in_pitch < w || !spl_ok(spl))
+        return FHT_EINVAL;
+    const int acc = acc_kind(in_t, acc_t);
+    if (acc < 0) return FHT_EINVAL;
+    const int in_elem = elem_of(in_t);
+    QuadPlan P = make_plan(h, w, q, false, in_elem, acc, false, true);
+    if (P.K > kMaxK) return FHT_EINVAL;
+    if (t_lo < 0 || t_hi < t_lo || t_hi >= P.n || out_pitch < P.W) return FHT_EINVAL;
+    const size_t need = plan_workspace(P);
+    if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
+    return run_sheared(P, img, in_elem, in_pitch, shear_fixed(spl), 0, t_lo, t_hi, out, acc_t,
+                       out_pitch, workspace, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------ scaled (Section 4)
+
+static bool alpha_ok(double alpha) { return alpha >= 1.0 / 256.0 && alpha <= 256.0; }
+
+// Source step D = ceil(2^32 / alpha) and scaled width ceil(w * 2^32 / D) of
+// a row of w pixels; false when the scaled row is empty or wider than the
+// library's largest side.
+static bool scaled_geometry(int w, double alpha, long long *step, int *w_alpha) {
+    if (!alpha_ok(alpha) || w < 1) return false;
+    const long long D = (long long)std::ceil(4294967296.0 / alpha);
+    const long long wa = (((long long)w << 32) + D - 1) / D;
+    if (D < 1 || wa < 1 || wa > kMaxSide) return false;
+    *step = D;
+    *w_alpha = (int)wa;
+    return true;
+}
+
+fht_status fht_scaled_width(int w, double alpha, int *w_alpha) {
+    long long D = 0;
+    if (!w_alpha || w > kMaxSide || !scaled_geometry(w, alpha, &D, w_alpha)) return FHT_EINVAL;
+    return FHT_OK;
+}
+
+fht_status fht_scaled_shape(int h, int w, fht_quadrant q, double alpha, int *rows, int *cols) {
+    if (!rows || !cols || !sizes_ok(h, w) || !quadrant_ok(q)) return FHT_EINVAL;
+    long long D = 0;
+    int wa = 0;
+    if (!scaled_geometry(q >= 2 ? h : w, alpha, &D, &wa)) return FHT_EINVAL;
+    *rows = next_pow2(q >= 2 ? w : h);
+    *cols = wa + *rows;
+    return FHT_OK;
+}
+
+fht_status fht_workspace_size_scaled(int h, int w, fht_quadrant q, double alpha, fht_dtype in_t,
+                                     fht_dtype acc_t, size_t *bytes) {
+    if (!sizes_ok(h, w) || !quadrant_ok(q) || !bytes) return FHT_EINVAL;
+    const int acc = acc_kind(in_t, acc_t);
+    if (acc < 0) return FHT_EINVAL;
+    long long D = 0;
+    int wa = 0;
+    if (!scaled_geometry(q >= 2 ? h : w, alpha, &D, &wa)) return FHT_EINVAL;
+    *bytes = plan_workspace(make_plan(h, w, q, false, elem_of(in_t), acc, false, true, 0, wa));
+    return FHT_OK;
+}
+
+fht_status fht_forward_scaled(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                              fht_quadrant q, double alpha, double spl, int t_lo, int t_hi,
+                              void *out, fht_dtype acc_t, int64_t out_pitch, void *workspace,
+                              size_t workspace_bytes, void *stream) {
+    if (!img || !out || !sizes_ok(h, w) || !quadrant_ok(q) || in_pitch < w || !spl_ok(spl))
+        return FHT_EINVAL;
+    const int acc = acc_kind(in_t, acc_t);
+    if (acc < 0) return FHT_EINVAL;
+    long long D = 0;
+    int wa = 0;
+    if (!scaled_geometry(q >= 2 ? h : w, alpha, &D, &wa)) return FHT_EINVAL;
+    const int in_elem = elem_of(in_t);
+    QuadPlan P = make_plan(h, w, q, false, in_elem, acc, false, true, 0, wa);
+    if (P.K > kMaxK) return FHT_EINVAL;
+    if (t_lo < 0 || t_hi < t_lo || t_hi >= P.n || out_pitch < P.W) return FHT_EINVAL;
+    const size_t need = plan_workspace(P);
+    if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
+    return run_sheared(P, img, in_elem, in_pitch, shear_fixed(spl), D, t_lo, t_hi, out, acc_t,
+                       out_pitch, workspace, (cudaStream_t)stream);
+}
+
+fht_status fht_scale_range(double phi_lo, double phi_hi, int h, int w, fht_quadrant *q,
+                           double *alpha, double *spl, int *t_lo, int *t_hi) {
+    if (!q || !alpha || !spl || !t_lo || !t_hi || !sizes_ok(h, w) || !(phi_lo <= phi_hi))
+        return FHT_EINVAL;
+    const double rad = M_PI / 180.0;
+    const double mid = 0.5 * (phi_lo + phi_hi);
+    int qq;
+    double a, b, edge;
+    if (mid >= -45.0 && mid <= 45.0 && phi_lo > -90.0 && phi_hi < 90.0) {
+        qq = FHT_Q0;
+        a = phi_lo;
+        b = phi_hi;
+        edge = std::tan(b * rad);
+    } else if (mid > 45.0 && mid <= 135.0 && phi_lo > 0.0 && phi_hi < 180.0) {
+        qq = FHT_Q3;
+        a = phi_lo - 90.0;
+        b = phi_hi - 90.0;
+        edge = std::tan(a * rad);
+    } else {
+        return FHT_EINVAL;
+    }
+    const double span = std::tan(b * rad) - std::tan(a * rad);
+    double al = 16.0;
+    if (span > 0) al = std::min(al, 1.0 / span);
+    if (edge != 0) al = std::min(al, 1.0 / std::fabs(edge));
+    int rows = 0, cols = 0;
+    fht_query_shape(h, w, (fht_quadrant)qq, &rows, &cols);
+    int hi = 0;
+    if (rows > 1) hi = std::min(rows - 1, (int)std::floor((rows - 1) * al * span + 1e-9));
+    *q = (fht_quadrant)qq;
+    *alpha = al;
+    *spl = qq == FHT_Q0 ? al * edge : -al * edge;
+    *t_lo = 0;
+    *t_hi = hi;
     return FHT_OK;
 }
 

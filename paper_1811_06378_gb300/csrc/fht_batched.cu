@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -33,6 +34,29 @@ constexpr int kDirectTables = 3;
 namespace {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// The batched tuning in force (fht_set_batched_tuning), read at plan creation.
+std::mutex g_btune_mu;
+fht_batched_tuning default_batched_tuning() {
+    fht_batched_tuning t{};
+    t.units_per_item = 4;
+    t.tile_u8 = 2;
+    t.tile_wide = 1;
+    t.ctas_per_sm = 2;
+    return t;
+}
+fht_batched_tuning g_btune = default_batched_tuning();
+
+bool batched_tuning_ok(const fht_batched_tuning &t) {
+    if (t.units_per_item < 1 || t.units_per_item > 16) return false;
+    if (t.tile_u8 < 1 || t.tile_u8 > 3 || t.tile_wide < 1 || t.tile_wide > 3) return false;
+    if (t.ctas_per_sm != 2 && t.ctas_per_sm != 3) return false;
+    for (int K = 7; K <= kMaxBatchK; ++K) {
+        const int f = t.first_levels[K];
+        if (f != 0 && (f < K - 6 || f > 6)) return false;
+    }
+    return true;
+}
 
 // One launchable work list (the forward transforms, or the adjoints, of the
 // batch) and its pinned staging. Workspace layout of a launch: the segment
@@ -106,6 +130,7 @@ struct fht_plan {
     std::vector<int> h, w, rows, cols;   // per image: size, and its quadrant's n x W
     long long wait_budget = 4000000000LL;   // ~2 s of SM clocks
     int dep_bias = 0;
+    int minb = 2;   // CTAs per SM of the kernel instantiation (tuning at creation)
     size_t last_counters_off = 0;   // counters of the table launched last
 };
 
@@ -116,7 +141,7 @@ namespace {
 // as in fht_adjoint: the opposite-sign transform of the gradient with cyclic
 // full-width levels, the final level cropped into the image gradient.
 fht_status build_table(const int *hs, const int *ws, int count, fht_quadrant q, bool f32,
-                       bool adjoint, Table &T) {
+                       bool adjoint, const fht_batched_tuning &tun, Table &T) {
     const bool u8 = !f32;
     std::vector<BatchSeg> segs;
     size_t level_bytes = 0, smem = 0;
@@ -142,8 +167,9 @@ fht_status build_table(const int *hs, const int *ws, int count, fht_quadrant q, 
             ms[0] = K;
             npass = 1;
         } else {
-            ms[0] = (K + 1) / 2;
-            ms[1] = K / 2;
+            // the tuning's split, else as even as possible (first pass larger)
+            ms[0] = tun.first_levels[K] ? tun.first_levels[K] : (K + 1) / 2;
+            ms[1] = K - ms[0];
             npass = 2;
         }
         // the one intermediate level (after pass 0): uint16 for uint8 images;
@@ -237,8 +263,10 @@ fht_status build_table(const int *hs, const int *ws, int count, fht_quadrant q, 
             }
             const bool u16_mid = u8 && p == 0;
             if (m >= 4) {
+                // block A has 2^(m-3) items per warp-column: widen the tile
+                // until every warp has one
                 const int rb = 1 << (m - 3);
-                d.n_a = std::max(u16_mid ? 2 : 1, 8 / rb);
+                d.n_a = std::max(u16_mid ? tun.tile_u8 : tun.tile_wide, 8 / rb);
             } else {
                 d.n_a = 1;
             }
@@ -255,7 +283,7 @@ fht_status build_table(const int *hs, const int *ws, int count, fht_quadrant q, 
                                                 : kVarU16Final);
             s.tiles = d.tiles;
             s.units = d.s_count * d.a_count * d.tiles;
-            s.chunk = std::max(1, std::min(kUnitsPerItem, s.units));
+            s.chunk = std::max(1, std::min(tun.units_per_item, s.units));
             s.lo_from_image = p == 0;
             s.hi_from_image = d.hi_final;
             s.lo_off = (int64_t)lvl_off;
@@ -407,15 +435,21 @@ fht_status fht_plan_create_batched(const int *hs, const int *ws, int count, fht_
         if (fht_query_shape(hs[j], ws[j], q, &r, &c) != FHT_OK) return FHT_EINVAL;
         if (r > (1 << kMaxBatchK)) return FHT_EUNSUPPORTED;
     }
+    fht_batched_tuning tun;
+    {
+        std::lock_guard<std::mutex> lk(g_btune_mu);
+        tun = g_btune;
+    }
     fht_plan *P = new (std::nothrow) fht_plan();
     if (!P) return FHT_ENOMEM;
     P->count = count;
     P->f32 = f32;
     P->q = q;
     P->sigma = (q == 0 || q == 3) ? 1 : -1;
-    fht_status s = build_table(hs, ws, count, q, f32, false, P->fwd);
+    P->minb = tun.ctas_per_sm;
+    fht_status s = build_table(hs, ws, count, q, f32, false, tun, P->fwd);
     if (s == FHT_OK && f32) {
-        s = build_table(hs, ws, count, q, true, true, P->adj);
+        s = build_table(hs, ws, count, q, true, true, tun, P->adj);
         P->has_adj = s == FHT_OK;
     }
     if (s != FHT_OK) {
@@ -447,8 +481,9 @@ fht_status fht_forward_batched(fht_plan *plan, const fht_image_desc *descs, void
             return FHT_EINVAL;
         calls[j] = CallPtrs{dj.img, dj.img_pitch, dj.out, dj.out_pitch};
     }
-    const Kernel k = plan->f32 ? (plan->sigma > 0 ? kernel_f32_pos() : kernel_f32_neg())
-                               : (plan->sigma > 0 ? kernel_u8_pos() : kernel_u8_neg());
+    const int mb = plan->minb;
+    const Kernel k = plan->f32 ? (plan->sigma > 0 ? kernel_f32_pos(mb) : kernel_f32_neg(mb))
+                               : (plan->sigma > 0 ? kernel_u8_pos(mb) : kernel_u8_neg(mb));
     return launch_table(plan, plan->fwd, calls.data(), k,
                         plan->f32 ? "batched_forward_f32" : "batched_forward_u8_i32", workspace,
                         stream);
@@ -467,8 +502,9 @@ fht_status fht_adjoint_batched(fht_plan *plan, const fht_adjoint_desc *descs, vo
             return FHT_EINVAL;
         calls[j] = CallPtrs{dj.grad_hough, dj.grad_hough_pitch, dj.grad_img, dj.grad_img_pitch};
     }
-    const Kernel k = plan->q == 0 ? kernel_adj_q0() : plan->q == 1 ? kernel_adj_q1()
-                   : plan->q == 2 ? kernel_adj_q2() : kernel_adj_q3();
+    const int mb = plan->minb;
+    const Kernel k = plan->q == 0 ? kernel_adj_q0(mb) : plan->q == 1 ? kernel_adj_q1(mb)
+                   : plan->q == 2 ? kernel_adj_q2(mb) : kernel_adj_q3(mb);
     return launch_table(plan, plan->adj, calls.data(), k, "batched_adjoint_f32", workspace,
                         stream);
 }
@@ -483,6 +519,21 @@ fht_status fht_batched_status(const fht_plan *plan, const void *workspace, void 
         cudaStreamSynchronize(st) != cudaSuccess)
         return FHT_ECUDA;
     return err == 0 ? FHT_OK : (fht_status)err;
+}
+
+fht_status fht_set_batched_tuning(const fht_batched_tuning *t) {
+    const fht_batched_tuning v = t ? *t : default_batched_tuning();
+    if (!batched_tuning_ok(v)) return FHT_EINVAL;
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    g_btune = v;
+    return FHT_OK;
+}
+
+fht_status fht_get_batched_tuning(fht_batched_tuning *out) {
+    if (!out) return FHT_EINVAL;
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    *out = g_btune;
+    return FHT_OK;
 }
 
 fht_status fht_batched_test_hooks(fht_plan *plan, long long wait_budget_cycles, int dep_bias) {

@@ -16,13 +16,6 @@ namespace batched {
 constexpr int kWarps = 8;
 constexpr int kMaxBatchK = 12;   // images up to 4096 rows (transposed: columns)
 constexpr int kMaxSegsShared = 2048;   // segment keys kept in shared memory
-// (group, tile) units per claimed item: the per-item bookkeeping (claim,
-// segment search, descriptor copy, dependency check, release) is paid once
-// for several units
-#ifndef FHT_BATCH_UNITS
-#define FHT_BATCH_UNITS 4
-#endif
-constexpr int kUnitsPerItem = FHT_BATCH_UNITS;
 
 // Kernel variants. uint8 -> int32: single-pass images, first passes into a
 // uint16 level, and int32 final passes from it. float: one variant per M.
@@ -94,8 +87,9 @@ __device__ __forceinline__ void run_item_m(int m, const PassDesc &d, int gy, int
 // Holding one claimed item ahead keeps the waits finite: the smallest
 // unfinished item is always some CTA's current item, and everything it
 // depends on has a smaller index.
-template <int MODE, int SG>
-__global__ void __launch_bounds__(kWarps * 32, 2)
+// MINB: CTAs per SM the register budget is sized for (2 or 3).
+template <int MODE, int SG, int MINB>
+__global__ void __launch_bounds__(kWarps * 32, MINB)
     batched_kernel(const BatchSeg *segs, int n_segs, int total_items, Counters *ctr,
                    unsigned int *done, long long wait_budget, int dep_bias) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -212,15 +206,15 @@ using Kernel = void (*)(const BatchSeg *, int, int, Counters *, unsigned int *, 
 
 // The instantiations, one per translation unit: forward transforms per type
 // and sign; adjoints per quadrant (sign, and whether the image gradient is
-// transposed).
-Kernel kernel_f32_pos();
-Kernel kernel_f32_neg();
-Kernel kernel_u8_pos();
-Kernel kernel_u8_neg();
-Kernel kernel_adj_q0();
-Kernel kernel_adj_q1();
-Kernel kernel_adj_q2();
-Kernel kernel_adj_q3();
+// transposed); each for 2 or 3 CTAs per SM (minb).
+Kernel kernel_f32_pos(int minb);
+Kernel kernel_f32_neg(int minb);
+Kernel kernel_u8_pos(int minb);
+Kernel kernel_u8_neg(int minb);
+Kernel kernel_adj_q0(int minb);
+Kernel kernel_adj_q1(int minb);
+Kernel kernel_adj_q2(int minb);
+Kernel kernel_adj_q3(int minb);
 
 }  // namespace batched
 }  // namespace fht

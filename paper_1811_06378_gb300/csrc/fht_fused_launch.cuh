@@ -23,13 +23,10 @@ constexpr size_t kMaxTileSmem = 227 * 1024;
 // Bytes a pass must read and write at least: its source level as stored
 // (image, or compact intermediate rows of the launched groups) and its
 // destination (intermediate rows, output slopes, or image gradient).
-// Whether a pass computes only part of its slopes (range pruning): forward
-// launches of such passes are named with a "_range" suffix so that
-// per-launch timings of range transforms and of whole quadrants can be told
-// apart.
-inline bool pass_pruned(const PassDesc &d, int M) {
-    return d.need_lo != 0 || d.need_hi != (1 << (d.k0 + M)) - 1;
-}
+// Launches of a range transform (PassDesc::range_call) are named with a
+// "_range" suffix so that per-launch timings of range transforms and of
+// whole quadrants can be told apart.
+inline const char *range_suffix(const PassDesc &d) { return d.range_call ? "_range" : ""; }
 
 inline double pass_alg_bytes(const PassDesc &d, int M, size_t src_bytes, size_t dst_bytes) {
     const double rows = (double)d.s_count * d.a_count * (1 << M);
@@ -162,8 +159,8 @@ cudaError_t launch_staged(PassDesc d, cudaStream_t st) {
         return e;
     const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
     const int grid = (int)(items < slots ? items : slots);
-    LaunchScope scope(pass_pruned(d, 6) ? "forward_fused_m6_i32_final_range"
-                                        : "forward_fused_m6_i32_final",
+    LaunchScope scope(d.range_call ? "forward_fused_m6_i32_final_range"
+                                   : "forward_fused_m6_i32_final",
                       st, pass_alg_bytes(d, 6, 2, 4));
     k<<<grid, 8 * 32, smem, st>>>(d, (int)items, tile_bytes);
     scope.done();
@@ -232,7 +229,7 @@ cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
              : OP == 2  ? "forward_min"
                         : "forward_fused",
              MA + MB, acc_name<Acc>(), d.hi_final ? "_final" : "", d.batch > 1 ? "_batch" : "",
-             !ADJ && pass_pruned(d, MA + MB) ? "_range" : "");
+             range_suffix(d));
     LaunchScope scope(name, st,
                       d.batch * pass_alg_bytes(d, MA + MB, sizeof(SrcE), sizeof(DstE)));
     k<<<grid, kFusedWarps * 32, smem, st>>>(d);

@@ -183,6 +183,59 @@ def test_sheared_bad_arguments_rejected_on_host(fht):
     assert L.fht_workspace_size_sheared(4096, 4096, 4, U8, I32, ctypes.byref(n)) == EINVAL
 
 
+@pytest.mark.parametrize("alpha", [1.0, 2.0, 3.0, 0.5, 0.25, 0.7, 1.37, 1.8660254037844386,
+                                   5.9, 1 / 3, 16.0])
+def test_scaled_geometry_matches_oracle(fht, alpha):
+    """The scaled width and shape (host) take the oracle's integer decisions:
+    the same double quotient, the same fixed-point step."""
+    for w in (1, 2, 7, 100, 301, 2048):
+        assert fht.scaled_width(w, alpha) == O.scaled_width(w, alpha)
+    for h, w in ((256, 100), (7, 300), (2048, 2048)):
+        for q in range(4):
+            n = O.next_pow2(w if O.TRANSPOSED[q] else h)
+            wa = O.scaled_width(h if O.TRANSPOSED[q] else w, alpha)
+            assert fht.scaled_shape(h, w, q, alpha) == (n, wa + n)
+
+
+@pytest.mark.parametrize("rng_", [(-15, 15), (75, 105), (-45, 45), (-60, 60), (10, 20),
+                                  (-20, -10), (80, 100), (100, 120), (-5, 5), (0, 0),
+                                  (20, 10), (-95, 0), (-85, 85), (30, 80)])
+@pytest.mark.parametrize("hw", [(2048, 2048), (256, 100), (1, 1), (7, 300)])
+def test_scale_range_matches_oracle(fht, rng_, hw):
+    want = O.scale_range(float(rng_[0]), float(rng_[1]), *hw)
+    if want is None:
+        with pytest.raises(fht.FHTError):
+            fht.scale_range(float(rng_[0]), float(rng_[1]), *hw)
+        return
+    got = fht.scale_range(float(rng_[0]), float(rng_[1]), *hw)
+    assert got[0] == want[0] and got[3:] == want[3:]
+    assert got[1] == want[1] and got[2] == want[2]   # the same double arithmetic
+
+
+def test_scaled_bad_arguments_rejected_on_host(fht):
+    L = fht.lib
+    fake, null, st = ctypes.c_void_p(0x10000), ctypes.c_void_p(0), ctypes.c_void_p(0)
+    U8, I32 = 0, 1
+    wa = ctypes.c_int()
+    assert L.fht_scaled_width(100, 0.0, ctypes.byref(wa)) == EINVAL
+    assert L.fht_scaled_width(100, float("nan"), ctypes.byref(wa)) == EINVAL
+    assert L.fht_scaled_width(100, 300.0, ctypes.byref(wa)) == EINVAL
+    assert L.fht_scaled_width(4096, 16.0, ctypes.byref(wa)) == EINVAL   # 65536 > 32768
+    assert L.fht_scaled_width(2048, 16.0, ctypes.byref(wa)) == 0 and wa.value == 32768
+    # 8 x 8 image, alpha 2: W = 16 + 8 = 24
+    args = lambda alpha, spl, lo, hi, pitch=24: (fake, U8, 8, 8, 8, 0, alpha, spl, lo, hi,  # noqa
+                                                 fake, I32, pitch, null, 0, st)
+    assert L.fht_forward_scaled(*args(2.0, 1.5, 0, 7)) == EINVAL
+    assert L.fht_forward_scaled(*args(0.0, 0.0, 0, 7)) == EINVAL
+    assert L.fht_forward_scaled(*args(2.0, 0.0, 3, 2)) == EINVAL
+    assert L.fht_forward_scaled(*args(2.0, 0.0, 0, 8)) == EINVAL
+    assert L.fht_forward_scaled(*args(2.0, 0.0, 0, 7, 23)) == EINVAL
+    n = ctypes.c_size_t()
+    assert L.fht_workspace_size_scaled(4096, 2048, 0, 2.0, U8, I32, ctypes.byref(n)) == 0
+    # two passes: one full-width level of n x W (W = 4096 + 4096), uint16
+    assert n.value == 4096 * 8192 * 2
+
+
 @pytest.mark.parametrize("q", [0, 1, 2, 3])
 @pytest.mark.parametrize("hw", [(9, 14), (16, 5), (1, 1), (33, 20)])
 def test_segment_matches_oracle(fht, q, hw):

@@ -116,3 +116,83 @@ def test_autotuner_picks_the_fastest_and_sets_it(fht):
         assert fht.get_tuning(9) == best
     finally:
         fht.set_tuning(9, *saved)
+
+
+BATCHED = [
+    {"ctas_per_sm": 3},
+    {"units_per_item": 1, "tile_u8": 1, "tile_wide": 3},
+    {"units_per_item": 16, "tile_u8": 3, "tile_wide": 2, "ctas_per_sm": 3},
+    {"first_levels": {7: 1, 8: 6, 9: 3, 10: 6, 11: 5, 12: 6}},
+    {"first_levels": {7: 6, 8: 2, 9: 6, 10: 4, 11: 6, 12: 6}, "ctas_per_sm": 3},
+]
+
+
+@pytest.mark.parametrize("bt", BATCHED)
+def test_batched_tunings_match_the_oracle(fht, bt):
+    """Every batched tuning the autotuner can pick (CTAs per SM, units per
+    item, tile widths, first-pass depth per size) gives the oracle's results
+    bit for bit: a uint8 batch of one- and two-pass images of every size
+    class up to 4096 rows, and an FP32 adjoint batch."""
+    from workloads import edge_batch
+    saved = fht.get_batched_tuning()
+    try:
+        fht.set_batched_tuning(None)
+        fht.set_batched_tuning(bt)
+        shapes = [(1, 1), (40, 70), (64, 64), (100, 300), (200, 129), (300, 90), (600, 1000),
+                  (1000, 77), (1500, 200), (4000, 33)]
+        imgs = [dev(a) for a in edge_batch(shapes, seed=77)]
+        plan = fht.BatchPlan(shapes, 1)
+        outs = plan.forward(imgs)
+        assert plan.status() == 0
+        for x, o in zip(imgs, outs):
+            assert (host(o) == i32(O.quadrant(x.cpu().numpy(), 1))).all(), tuple(x.shape)
+        fshapes = shapes[:8]
+        fplan = fht.BatchPlan(fshapes, 2, torch.float32, torch.float32)
+        rng = np.random.default_rng(78)
+        grads = [dev(rng.standard_normal(sh).astype(np.float32)) for sh in fplan.out_shapes]
+        gouts = fplan.adjoint(grads)
+        assert fplan.status() == 0
+        for (h, w), g, o in zip(fshapes, grads, gouts):
+            want = O.adjoint_quadrant(g.cpu().numpy(), h, w, 2, "f32")
+            assert np.array_equal(host(o), want), (h, w)
+    finally:
+        fht.set_batched_tuning(None)
+        fht.set_batched_tuning(saved)
+
+
+def test_batched_autotuner_keeps_results_and_sets_the_best(fht):
+    """A short batched sweep on a small batch: every candidate's results
+    equal the default's (checked inside), the best is left in force and the
+    default's time is reported."""
+    from paper_1811_06378_gb300 import autotune
+    saved = fht.get_batched_tuning()
+    try:
+        res = autotune.tune_batched(count=24, seed=5, reps=2, warmup=1)
+        assert res["us"] <= res["default_us"]
+        got = fht.get_batched_tuning()
+        want = res["tuning"]
+        assert got["ctas_per_sm"] == want["ctas_per_sm"]
+        assert got["units_per_item"] == want["units_per_item"]
+        assert {str(k): v for k, v in got["first_levels"].items()} == want["first_levels"]
+    finally:
+        fht.set_batched_tuning(None)
+        fht.set_batched_tuning(saved)
+
+
+def test_batched_tuning_changes_the_plan_workspace(fht):
+    """The first pass's depth sets the intermediate level's compact width:
+    for one 1024 x 300 uint8 image (K = 10), w_c + 2^f columns (pitch
+    rounded to 64) of uint16, plus the plan's fixed tables."""
+    saved = fht.get_batched_tuning()
+    sizes = {}
+    try:
+        for f in (4, 5, 6):
+            fht.set_batched_tuning(None)
+            fht.set_batched_tuning({"first_levels": {10: f}})
+            sizes[f] = fht.BatchPlan([(1024, 300)], 0).workspace_bytes
+    finally:
+        fht.set_batched_tuning(None)
+        fht.set_batched_tuning(saved)
+    pitch = lambda f: -(-(300 + (1 << f)) // 64) * 64   # noqa: E731
+    assert sizes[5] - sizes[4] == 1024 * (pitch(5) - pitch(4)) * 2
+    assert sizes[6] - sizes[5] == 1024 * (pitch(6) - pitch(5)) * 2

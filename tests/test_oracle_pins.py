@@ -621,3 +621,147 @@ def test_min_is_negated_max_of_negated_image():
         assert (O.quadrant_op(img, q, 2) == -O.quadrant_op(-img, q, 1)).all()
         f = img.astype(np.float32) / 7
         assert (O.quadrant_op(f, q, 2, "f32") == -O.quadrant_op(-f, q, 1, "f32")).all()
+
+
+# --------------------------------------------------------------- scale (Section 4)
+
+def test_scale_columns_replicate_and_subsample():
+    """Column x' of the row scaled by alpha is column floor(x'/alpha): an
+    integer factor k repeats every column k times (np.repeat), 1/k keeps
+    every k-th column, 1 is the identity; the scaled width counts the
+    columns whose source lies inside the row."""
+    img = random_image(9, 13, "u8", seed=5)
+    for k in (2, 3, 5, 7):
+        assert np.array_equal(O.scaled_image(img, float(k)), np.repeat(img, k, axis=1))
+        assert O.scaled_width(13, float(k)) == 13 * k
+    for k in (2, 4, 8):
+        assert np.array_equal(O.scaled_image(img, 1.0 / k), img[:, ::k])
+        assert O.scaled_width(13, 1.0 / k) == -(-13 // k)
+    assert np.array_equal(O.scaled_image(img, 1.0), img)
+    # any factor: monotone, steps of floor(1/alpha) or ceil(1/alpha) source
+    # columns, within one column of x'/alpha, and every source column < w
+    for alpha in (0.3, 0.7, 1.37, 2.5, 5.9):
+        src = O.scale_columns(101, alpha)
+        assert src[0] == 0 and src[-1] < 101
+        assert abs(src - np.floor(np.arange(len(src)) / alpha)).max() <= 1
+        assert set(np.unique(np.diff(src))) <= {math.floor(1 / alpha), math.ceil(1 / alpha)}
+        assert O.scale_columns(101, alpha).size == O.scaled_width(101, alpha)
+        assert (O.scaled_width(101, alpha) * O.scale_step(alpha)) >> 32 >= 101
+
+
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
+def test_scale_one_is_the_plain_quadrant(q):
+    img = random_image(37, 21, "u8", seed=q)
+    assert (O.scaled_quadrant(img, q, 1.0) == O.quadrant(img, q)).all()
+    assert (O.scaled_quadrant(img, q, 1.0, 0.4) == O.sheared_quadrant(img, q, 0.4)).all()
+
+
+@pytest.mark.parametrize("q,alpha,spl", [(0, 2.0, 0.0), (1, 3.0, -0.3), (2, 0.5, 0.6),
+                                         (3, 0.25, -1.0), (0, 0.5, 1.0), (3, 2.0, 0.45)])
+def test_scaled_quadrant_equals_brute_force_sums(q, alpha, spl):
+    """Every point is the sum along the pattern over the scaled, sheared
+    image, written out with the closed-form offsets and the real-number
+    source column floor(c/alpha) (exact for these factors): H[t][x] =
+    sum_y I[y][floor(c/alpha)] at c = (x + sigma*off(t, y) - s(y)) mod W when
+    c < w_alpha, with W = w_alpha + n. No butterfly, no resampled array."""
+    img = random_image(10, 7, "u8", seed=11)
+    h, w = img.shape
+    src = img.T if O.TRANSPOSED[q] else img
+    rows, cols = src.shape
+    n = O.next_pow2(rows)
+    wa = math.ceil(cols * alpha - 1e-12)   # columns x' with floor(x'/alpha) < cols
+    W = wa + n
+    sg = O.SIGMA[q]
+    # the per-row shifts as pinned by test_shear_shifts_round_half_up (exact
+    # halves such as 5 * -0.3 + 1/2 follow the fixed-point spl)
+    s = [int(v) for v in O.shear_shifts(rows, spl)]
+    H = np.zeros((n, W), np.int64)
+    for t in range(n):
+        for x in range(W):
+            acc = 0
+            for y in range(rows):
+                c = (x + sg * O.offset(n, t, y) - s[y]) % W
+                if c < wa:
+                    acc += int(src[y, int(math.floor(c / alpha + 1e-12))])
+            H[t, x] = acc
+    got = O.scaled_quadrant(img, q, alpha, spl)
+    assert got.shape == (n, W)
+    assert (got == H).all()
+
+
+@pytest.mark.parametrize("q", [0, 1, 2, 3])
+def test_scaled_rows_sum_to_the_scaled_mass(q):
+    """Every slope row of the scaled quadrant (no shear) sums to the mass of
+    the scaled image: each of its pixels lies on exactly one pattern per row
+    (the mass invariant of the plain quadrant, on the resampled image)."""
+    img = random_image(45, 30, "u8", seed=20 + q)
+    src = img.T if O.TRANSPOSED[q] else img
+    for alpha in (0.6, 1.8, 3.0):
+        H = O.scaled_quadrant(img, q, alpha)
+        mass = int(O.scaled_image(src, alpha).astype(np.int64).sum())
+        assert (H.sum(axis=1) == mass).all()
+
+
+def test_scaled_line_lands_on_the_45_degree_row():
+    """Section 4: scaling by alpha turns a line at tg(beta) = 1/alpha into one
+    at 45 degrees. A line with dx/dy = 1/2 (one column every second row),
+    scaled by 2, is a two-pixel-wide staircase whose left edge is the exact
+    diagonal, which the slope n-1 pattern (off(n-1, y) = y) follows: that
+    Hough point sums one pixel of every row."""
+    n, x0 = 64, 5
+    img = np.zeros((n, n), np.uint8)
+    for y in range(n):
+        img[y, x0 + y // 2] = 1
+    H = O.scaled_quadrant(img, 0, 2.0)
+    assert H[n - 1, 2 * x0] == n
+    assert H.max() == n
+    assert np.unravel_index(np.argmax(H[:, 2 * x0]), (n,))[0] == n - 1
+
+
+@pytest.mark.parametrize("phi", [-14.0, -6.5, 0.0, 3.0, 11.0, 15.0])
+def test_scale_range_finds_lines_at_their_angle(phi):
+    """The [-15, 15] degree range as one scaled and sheared quadrant: alpha
+    = 1/(2 tan 15) stretches it over every slope row (spl = 1/2), so its
+    angles are resolved 1.87 times finer than with the shear alone; a
+    rasterised line at phi peaks at the row whose angle is phi within about
+    one of those finer steps, and the last row is the range's lower end."""
+    n = 256
+    q, alpha, spl, t_lo, t_hi = O.scale_range(-15.0, 15.0, n, n)
+    assert q == 0 and t_lo == 0 and t_hi == n - 1
+    assert alpha == pytest.approx(1 / (2 * math.tan(math.radians(15.0))))
+    assert spl == pytest.approx(0.5)
+    ang = lambda t: math.degrees(math.atan((spl - t / (n - 1)) / alpha))  # noqa: E731
+    assert ang(0) == pytest.approx(15.0) and ang(n - 1) == pytest.approx(-15.0)
+    img = np.zeros((n, n), np.uint8)
+    k = -math.tan(math.radians(phi))
+    x0 = n / 2 - k * n / 2
+    for y in range(n):
+        img[y, int(math.floor(x0 + k * y + 0.5))] = 1
+    H = O.scaled_quadrant(img, q, alpha, spl, t_lo=t_lo, t_hi=t_hi)
+    t_pk = int(np.unravel_index(np.argmax(H), H.shape)[0])
+    step = math.degrees(math.atan(1 / ((n - 1) * alpha)))
+    assert abs(ang(t_pk) - phi) <= 2.5 * step
+    assert H.max() >= 0.5 * n
+
+
+def test_scale_range_choices():
+    """Symmetric ranges fill the quadrant with spl = 1/2; an off-axis narrow
+    range is stretched until its far end reaches the unit shear; mostly
+    horizontal ranges go to Q3; the paper's arctg(1/2) neighbourhood of zero
+    needs no scale (alpha = 1, spl = 1/2)."""
+    for g in (5.0, 20.0, 40.0, 60.0):
+        q, alpha, spl, t_lo, t_hi = O.scale_range(-g, g, 512, 512)
+        assert q == 0 and spl == pytest.approx(0.5) and t_hi == 511
+        assert alpha == pytest.approx(min(16.0, 1 / (2 * math.tan(math.radians(g)))))
+    g = math.degrees(math.atan(0.5))
+    q, alpha, spl, _, t_hi = O.scale_range(-g, g, 512, 512)
+    assert alpha == pytest.approx(1.0) and spl == pytest.approx(0.5) and t_hi == 511
+    q, alpha, spl, _, t_hi = O.scale_range(10.0, 20.0, 512, 512)
+    assert q == 0 and spl == pytest.approx(1.0)
+    assert alpha == pytest.approx(1 / math.tan(math.radians(20.0)))
+    assert t_hi == math.floor(511 * alpha * (math.tan(math.radians(20.0)) -
+                                             math.tan(math.radians(10.0))) + 1e-9)
+    q, alpha, spl, _, t_hi = O.scale_range(80.0, 100.0, 300, 600)
+    assert q == 3 and spl == pytest.approx(0.5) and t_hi == O.quadrant_geometry(300, 600, 3)[0] - 1
+    assert O.scale_range(20.0, 10.0, 64, 64) is None
+    assert O.scale_range(-95.0, 0.0, 64, 64) is None

@@ -126,3 +126,43 @@ def test_forward_workspace_matches_the_layout_model(fht, restore, levels):
             for acc, u16 in ((torch.int32, True), (torch.float32, False)):
                 got = fht.workspace_size(h, w, fht.LAYOUT_QUADRANT, q, torch.uint8, acc)
                 assert got == _model_forward_workspace(h, w, q, levels, u16), (h, w, q, acc)
+
+
+@pytest.fixture
+def restore_batched(fht):
+    saved = fht.get_batched_tuning()
+    yield
+    fht.set_batched_tuning(None)
+    fht.set_batched_tuning(saved)
+
+
+def test_batched_tuning_set_get_and_checks(fht, restore_batched):
+    fht.set_batched_tuning(None)
+    d = fht.get_batched_tuning()
+    assert d == {"units_per_item": 4, "tile_u8": 2, "tile_wide": 1, "ctas_per_sm": 2,
+                 "first_levels": {}}
+    fht.set_batched_tuning({"units_per_item": 8, "ctas_per_sm": 3, "first_levels": {10: 6}})
+    got = fht.get_batched_tuning()
+    assert got["units_per_item"] == 8 and got["ctas_per_sm"] == 3
+    assert got["first_levels"] == {10: 6} and got["tile_u8"] == 2
+    for bad in ({"units_per_item": 0}, {"units_per_item": 17}, {"tile_u8": 4},
+                {"tile_wide": 0}, {"ctas_per_sm": 1}, {"ctas_per_sm": 4},
+                {"first_levels": {10: 3}}, {"first_levels": {7: 7}}):
+        with pytest.raises(fht.FHTError):
+            fht.set_batched_tuning(bad)
+        assert fht.get_batched_tuning() == got   # a rejected tuning changes nothing
+    fht.set_batched_tuning(None)
+    assert fht.get_batched_tuning() == d
+
+
+def test_table_with_batched_part_is_applied(fht, restore, restore_batched, tmp_path):
+    from paper_1811_06378_gb300 import autotune
+    table = {"table": {}, "batched": {"tuning": {"units_per_item": 2, "tile_u8": 1,
+                                                 "tile_wide": 3, "ctas_per_sm": 3,
+                                                 "first_levels": {"9": 4}},
+                                      "us": 1.0, "default_us": 2.0}}
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps(table))
+    autotune.load(str(path))
+    assert fht.get_batched_tuning() == {"units_per_item": 2, "tile_u8": 1, "tile_wide": 3,
+                                        "ctas_per_sm": 3, "first_levels": {9: 4}}
