@@ -356,6 +356,48 @@ fht_status fht_forward_scaled(const void *img, fht_dtype in_t, int h, int w, int
 fht_status fht_scale_range(double phi_lo, double phi_hi, int h, int w, fht_quadrant *q,
                            double *alpha, double *spl, int *t_lo, int *t_hi);
 
+/* ------------------------------------------------------------ one image over P GPUs
+ * Not in the paper: how one quadrant splits over P = 2, 4 or 8 ranks by rows
+ * (by columns of the original image for Q2/Q3). With n = 2^K slope rows and
+ * W columns (fht_query_shape of the whole image), rank p holds the image rows
+ * [p*n/P, (p+1)*n/P) (those below the image are absent: an empty or short
+ * strip), and:
+ *   1. fht_forward_padded: its strip's K - log2(P) levels, i.e. the strip's
+ *      quadrant padded to n_s = n/P rows on the whole image's cyclic width W:
+ *      n_s x W, row tau = the strip's slope tau;
+ *   2. one all-to-all: rank b receives rows [b*n_s/P, (b+1)*n_s/P) of every
+ *      strip's result (n_s/P x W per pair);
+ *   3. fht_merge_strips: the last log2(P) levels on those rows, giving the
+ *      quadrant's slope rows [b*n/P, (b+1)*n/P), bit for bit what one GPU
+ *      computes (the same additions in the same order).
+ * The Python package's `sharded` module runs the three steps over
+ * torch.distributed. */
+
+/* Workspace bytes of fht_forward_padded. */
+fht_status fht_workspace_size_padded(int h, int w, fht_quadrant q, int n, int W,
+                                     fht_dtype in_t, fht_dtype acc_t, size_t *bytes);
+
+/* Quadrant q of the h x w image zero-padded to n rows (of the transposed image
+ * for Q2/Q3; n a power of two, n >= those rows) and taken on the cyclic width
+ * W >= w_c + n (w_c = w for Q0/Q1, h for Q2/Q3): n x W into out (pitch
+ * out_pitch >= W); types as fht_forward. With n = next_pow2(rows) and
+ * W = w_c + n this is fht_forward. The strip's row count may be 0 (an empty
+ * strip: out is zeroed). */
+fht_status fht_forward_padded(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                              fht_quadrant q, int n, int W, void *out, fht_dtype acc_t,
+                              int64_t out_pitch, void *workspace, size_t workspace_bytes,
+                              void *stream);
+
+/* The last log2(strips) levels (strips = P = 1, 2, 4 or 8) for the slopes
+ * tau = tau0 .. tau0 + rows - 1: parts holds, for each strip p, its level
+ * rows tau (rows x W, pitch in_pitch) at parts + p * part_stride (elements);
+ * out receives rows tau*P + c (c < P) at row (tau - tau0)*P + c (rows*P x W,
+ * pitch out_pitch). dtype FHT_I32 or FHT_F32 (the accumulator); the sign is
+ * quadrant q's. */
+fht_status fht_merge_strips(const void *parts, fht_dtype dtype, int strips, int rows, int W,
+                            int64_t part_stride, int64_t in_pitch, int tau0, fht_quadrant q,
+                            void *out, int64_t out_pitch, void *stream);
+
 /* ------------------------------------------------------------ uniform batches
  * `batch` transforms of the same size and layout in one launch per pass (the
  * launch's third grid dimension is the image), so that many small images fill

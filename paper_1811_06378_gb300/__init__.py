@@ -29,6 +29,7 @@ __all__ = [
     "workspace_size_many", "forward_many", "adjoint_many",
     "workspace_size_sheared", "shear_range", "forward_sheared",
     "scaled_width", "scaled_shape", "workspace_size_scaled", "scale_range", "forward_scaled",
+    "workspace_size_padded", "forward_padded", "merge_strips",
     "BatchPlan", "FHT_OK", "FHT_ETIMEOUT",
 ]
 
@@ -92,6 +93,9 @@ def _load() -> ctypes.CDLL:
         "fht_workspace_size_scaled": (i, [i, i, i, d, i, i, ctypes.POINTER(sz)]),
         "fht_forward_scaled": (i, [vp, i, i, i, i64, i, d, d, i, i, vp, i, i64, vp, sz, vp]),
         "fht_scale_range": (i, [d, d, i, i, ip, ctypes.POINTER(d), ctypes.POINTER(d), ip, ip]),
+        "fht_workspace_size_padded": (i, [i, i, i, i, i, i, i, ctypes.POINTER(sz)]),
+        "fht_forward_padded": (i, [vp, i, i, i, i64, i, i, i, vp, i, i64, vp, sz, vp]),
+        "fht_merge_strips": (i, [vp, i, i, i, i, i64, i64, i, i, vp, i64, vp]),
         "fht_plan_create_batched": (i, [ctypes.POINTER(i), ctypes.POINTER(i), i, i, i, i,
                                         ctypes.POINTER(vp), ctypes.POINTER(sz)]),
         "fht_forward_batched": (i, [vp, vp, vp, sz, vp]),
@@ -205,7 +209,8 @@ def load_tuning(path: str) -> dict:
         res = json.load(f)
     for k, e in res["table"].items():
         set_tuning(int(k), int(e["max_levels"]), int(e["tile_u8"]), int(e["tile_wide"]))
-    if "batched" in res:
+    if "batched" in res:   # replaces the batched tuning in force
+        set_batched_tuning(None)
         set_batched_tuning(res["batched"]["tuning"])
     return res
 
@@ -528,6 +533,63 @@ def forward_scaled(img: torch.Tensor, q: int, alpha: float, spl: float = 0.0, t_
                                   float(spl), t_lo, t_hi, _ptr(out), out_code, out_pitch,
                                   _ptr(ws), _nbytes(ws), _stream(stream)),
            "fht_forward_scaled")
+    return out
+
+
+# ------------------------------------------------------------------ strips of one image
+
+def workspace_size_padded(h: int, w: int, q: int, n: int, W: int, in_dtype: torch.dtype,
+                          acc: torch.dtype) -> int:
+    b = ctypes.c_size_t()
+    _check(lib.fht_workspace_size_padded(h, w, q, n, W, _DTYPE[in_dtype], _DTYPE[acc],
+                                         ctypes.byref(b)), "fht_workspace_size_padded")
+    return b.value
+
+
+def forward_padded(img: torch.Tensor, q: int, n: int, W: int, acc: torch.dtype = torch.int32,
+                   out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """Quadrant q of img zero-padded to n rows (of the transposed image for
+    Q2/Q3) on the cyclic width W: (n, W) (fht_forward_padded). img may have
+    no rows (an empty strip)."""
+    h, w = img.shape
+    if out is None:
+        out = torch.empty((n, W), dtype=acc, device=img.device)
+    out_code, out_pitch = _dev2d(out, "out")
+    _shape(out, (n, W), "out")
+    if img.numel() == 0:
+        _check(lib.fht_forward_padded(None, _DTYPE[img.dtype], h, w, max(w, 1), q, n, W,
+                                      _ptr(out), out_code, out_pitch, None, 0, _stream(stream)),
+               "fht_forward_padded")
+        return out
+    in_code, in_pitch = _dev2d(img, "img")
+    ws = _workspace(workspace, workspace_size_padded(h, w, q, n, W, img.dtype, out.dtype),
+                    img.device)
+    _check(lib.fht_forward_padded(_ptr(img), in_code, h, w, in_pitch, q, n, W, _ptr(out),
+                                  out_code, out_pitch, _ptr(ws), _nbytes(ws), _stream(stream)),
+           "fht_forward_padded")
+    return out
+
+
+def merge_strips(parts: torch.Tensor, q: int, tau0: int, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """The last log2(P) levels of a sharded quadrant (fht_merge_strips):
+    parts (P, rows, W) holds every strip's level rows tau0 .. tau0+rows-1;
+    returns (rows*P, W), row (tau - tau0)*P + c = final slope tau*P + c."""
+    P, rows, W = parts.shape
+    if parts.dtype not in (torch.int32, torch.float32) or not parts.is_cuda:
+        raise ValueError("parts: int32 or float32 CUDA tensor")
+    if parts.stride(2) != 1:
+        raise ValueError("parts: unit column stride")
+    if out is None:
+        out = torch.empty((rows * P, W), dtype=parts.dtype, device=parts.device)
+    out_code, out_pitch = _dev2d(out, "out")
+    _shape(out, (rows * P, W), "out")
+    if out.dtype != parts.dtype:
+        raise ValueError("out: same dtype as parts")
+    _check(lib.fht_merge_strips(_ptr(parts), _DTYPE[parts.dtype], P, rows, W,
+                                parts.stride(0), parts.stride(1), tau0, q, _ptr(out),
+                                out_pitch, _stream(stream)), "fht_merge_strips")
     return out
 
 

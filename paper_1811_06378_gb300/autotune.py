@@ -199,7 +199,8 @@ def load(path_or_result) -> dict:
         return fht.load_tuning(os.fspath(path_or_result))
     for k, e in path_or_result["table"].items():
         fht.set_tuning(int(k), int(e["max_levels"]), int(e["tile_u8"]), int(e["tile_wide"]))
-    if "batched" in path_or_result:
+    if "batched" in path_or_result:   # replaces the batched tuning in force
+        fht.set_batched_tuning(None)
         fht.set_batched_tuning(path_or_result["batched"]["tuning"])
     return path_or_result
 

@@ -146,8 +146,13 @@ struct QuadPlan {
 // 4), also on cyclic full-width levels: the shear moves the black zone, so
 // the compact columns do not hold. w_scaled > 0 replaces the content width
 // (columns of the (transposed) image) by that of its scaled rows (Section 4).
+// n_rows > 0 pads the (transposed) image to that many rows instead of the
+// next power of two of its height, and W_cols > 0 sets the cyclic width (a
+// strip of a sharded image is transformed with the whole image's n_s rows
+// and width).
 QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
-                   bool adjoint = false, bool sheared = false, int op = 0, int w_scaled = 0) {
+                   bool adjoint = false, bool sheared = false, int op = 0, int w_scaled = 0,
+                   int n_rows = 0, int W_cols = 0) {
     QuadPlan P{};
     P.q = q;
     P.adjoint = adjoint;
@@ -160,7 +165,7 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
     P.h_c = P.transpose ? w : h;
     P.w_c = P.transpose ? h : w;
     if (w_scaled > 0) P.w_c = w_scaled;
-    P.n = next_pow2(P.h_c);
+    P.n = n_rows > 0 ? n_rows : next_pow2(P.h_c);
     P.K = ilog2(P.n);
     if (full) {
         P.W = next_pow2(h) + next_pow2(w);
@@ -169,6 +174,7 @@ QuadPlan make_plan(int h, int w, int q, bool full, int in_elem, int acc_elem,
         P.W = P.w_c + P.n;
         P.w_in = P.w_c;
     }
+    if (W_cols > 0) P.W = W_cols;
     P.tuned = op == 0 && !sheared;
     P.npass = split_levels(P.K, P.m, P.tuned ? tuning_for(P.K).max_levels : kMaxLevelsPerPass);
     P.k[0] = 0;
@@ -770,6 +776,58 @@ static fht_status forward_common(const void *img, fht_dtype in_t, int h, int w,
     Side o{out, out_pitch, elem_of(acc_t), 0, P.W};
     return run_forward(P, image, o, quadrant_map(t_lo, t_hi), t_lo, t_hi, acc, ws,
                        (cudaStream_t)stream, Batch{}, t_lo != 0 || t_hi != P.n - 1);
+}
+
+// ------------------------------------------------------------ strips of a sharded image
+
+// Rows (h_c) and columns (w_c) of the (transposed) strip, and whether n and W
+// fit it: n a power of two >= h_c (up to 2^kMaxK), W >= w_c + n.
+static bool padded_ok(int h, int w, fht_quadrant q, int n, int W, int *h_c, int *w_c) {
+    if (!quadrant_ok(q) || h < 0 || w < 0 || h > kMaxSide || w > kMaxSide) return false;
+    *h_c = q >= 2 ? w : h;
+    *w_c = q >= 2 ? h : w;
+    if (*w_c < 1 || n < 1 || (n & (n - 1)) != 0 || ilog2(n) > kMaxK || n < *h_c) return false;
+    return W >= *w_c + n && W <= 2 * kMaxSide;
+}
+
+fht_status fht_workspace_size_padded(int h, int w, fht_quadrant q, int n, int W, fht_dtype in_t,
+                                     fht_dtype acc_t, size_t *bytes) {
+    int h_c = 0, w_c = 0;
+    if (!bytes || !padded_ok(h, w, q, n, W, &h_c, &w_c)) return FHT_EINVAL;
+    const int acc = acc_kind(in_t, acc_t);
+    if (acc < 0) return FHT_EINVAL;
+    *bytes = h_c == 0 ? 0
+                      : plan_workspace(make_plan(h, w, q, false, elem_of(in_t), acc, false,
+                                                 false, 0, 0, n, W));
+    return FHT_OK;
+}
+
+fht_status fht_forward_padded(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,
+                              fht_quadrant q, int n, int W, void *out, fht_dtype acc_t,
+                              int64_t out_pitch, void *workspace, size_t workspace_bytes,
+                              void *stream) {
+    int h_c = 0, w_c = 0;
+    if (!out || !padded_ok(h, w, q, n, W, &h_c, &w_c) || out_pitch < W) return FHT_EINVAL;
+    const int acc = acc_kind(in_t, acc_t);
+    if (acc < 0) return FHT_EINVAL;
+    if (h_c == 0) {
+        // an empty strip: every level, and so the result, is zero
+        const cudaError_t e = cudaMemset2DAsync(out, (size_t)out_pitch * 4, 0, (size_t)W * 4, n,
+                                                (cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            g_last_cuda_error = (int)e;
+            return FHT_ECUDA;
+        }
+        return FHT_OK;
+    }
+    if (!img || in_pitch < w) return FHT_EINVAL;
+    QuadPlan P = make_plan(h, w, q, false, elem_of(in_t), acc, false, false, 0, 0, n, W);
+    const size_t need = plan_workspace(P);
+    if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
+    Side image{const_cast<void *>(img), in_pitch, elem_of(in_t), P.h_c, P.w_c};
+    Side o{out, out_pitch, elem_of(acc_t), 0, P.W};
+    return run_forward(P, image, o, quadrant_map(0, P.n - 1), 0, P.n - 1, acc, workspace,
+                       (cudaStream_t)stream);
 }
 
 fht_status fht_forward(const void *img, fht_dtype in_t, int h, int w, int64_t in_pitch,

@@ -490,10 +490,12 @@ __device__ __forceinline__ T ldscalar(const T *p) {
 // column (c * scale_step) >> 32 (of image row y; for the transposed
 // quadrants, image column y of that image row), and zero otherwise. The
 // source columns are not contiguous (repeated or skipped), so each element
-// is its own load.
+// is its own load. Out of line: the adjoint kernels share this pass code, and
+// the gathers would otherwise grow their hot loop.
 template <int SG, int RA, typename Acc, typename SrcE, bool NC = true>
-__device__ __forceinline__ void load_block_a_scaled(const PassDesc &d, int row0, int X,
-                                                    Acc (&v)[RA][kV]) {
+__device__ __noinline__ Block<Acc, RA> load_block_a_scaled(const PassDesc &d, int row0, int X) {
+    Block<Acc, RA> b;
+    auto &v = b.x;
     const SrcE *img = reinterpret_cast<const SrcE *>(d.lo.ptr);
     const unsigned long long step = (unsigned long long)d.scale_step;
 #pragma unroll
@@ -518,6 +520,7 @@ __device__ __forceinline__ void load_block_a_scaled(const PassDesc &d, int row0,
         }
         if constexpr (SG < 0) reverse8(v[r]);
     }
+    return b;
 }
 
 // Block A's RA source rows s0.. for this lane's 8 buffer columns i0..i0+7.
@@ -535,7 +538,12 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
             const int p_first = A_off + sg * i0;
             const int X = (sg > 0 ? p_first : p_first - (kV - 1)) - splus;
             if (d.scale_step) {
-                load_block_a_scaled<SG, RA, Acc, SrcE, NC>(d, S * (1 << M) + s0, X, v);
+                const Block<Acc, RA> b =
+                    load_block_a_scaled<SG, RA, Acc, SrcE, NC>(d, S * (1 << M) + s0, X);
+#pragma unroll
+                for (int r = 0; r < RA; ++r)
+#pragma unroll
+                    for (int k = 0; k < kV; ++k) v[r][k] = b.x[r][k];
                 return;
             }
             // ascending columns of the whole warp item: [Xw0, Xw1)
@@ -1033,6 +1041,27 @@ __device__ __forceinline__ bool sheared_tile_zero(const PassDesc &d, int M, int 
     return !(j < len || j + T > d.W);
 }
 
+// Windowed adjoint level: does any of the 2^M rows of group (S, a) keep a
+// column of the tile [p0, p0 + T)? (the same test as win_rows_hit, over the
+// whole group, in a loop: a tile no row keeps is skipped whole). The rows'
+// windows move by sigma*S per slope, so for small S they cover little more
+// than one window length and most tiles of the row are never read.
+__device__ __forceinline__ bool group_window_hit(const PassDesc &d, int M, int S, int a, int p0,
+                                                 int T) {
+    const int W = d.W, L = d.win_len, k1 = d.k0 + M, mask = (1 << k1) - 1;
+    if (p0 >= W) return false;
+    const int len = T < W - p0 ? T : W - p0;
+    const int row0 = hi_row(d, M, S, a, 0);
+#pragma unroll 1
+    for (int c = 0; c < (1 << M); ++c) {
+        const int row = row0 + c;
+        int j = p0 - win_base(d, row >> k1, row & mask);
+        if (j < 0) j += W;
+        if (j < L || j + len > W) return true;
+    }
+    return false;
+}
+
 // Where one (group, tile) item of a pass sits: its group (S, a), first
 // output column p0, the buffer column offsets of its source (A_off) and
 // destination (D), and whether the whole tile is black (all zero).
@@ -1050,7 +1079,8 @@ __device__ __forceinline__ ItemPos item_pos(const PassDesc &d, int T, int gy, in
     ip.A_off = SG > 0 ? ip.p0 - (1 << (d.k0 + M)) + (1 << d.k0) : ip.p0 + T - 1;
     ip.D = SG > 0 ? ip.p0 : ip.p0 + T - 1;
     if constexpr (ADJ && !FIN)
-        ip.black = d.shear_on && d.lo_image && sheared_tile_zero(d, M, ip.S, ip.p0, T);
+        ip.black = (d.shear_on && d.lo_image && sheared_tile_zero(d, M, ip.S, ip.p0, T)) ||
+                   (d.hi_win && !group_window_hit(d, M, ip.S, ip.a, ip.p0, T));
     else
         ip.black = !ADJ && FIN && tile_all_black(d, M, ip.a, ip.p0, T);
     return ip;

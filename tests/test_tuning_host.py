@@ -79,9 +79,16 @@ def test_shipped_table_is_valid(fht, restore):
     import os
     if not os.path.exists(fht.TUNING_FILE):
         pytest.skip("no shipped table")
+    saved_b = fht.get_batched_tuning()
     res = fht.load_tuning(fht.TUNING_FILE)
     for k, e in res["table"].items():
         assert fht.get_tuning(int(k)) == (e["max_levels"], e["tile_u8"], e["tile_wide"])
+    if "batched" in res:
+        want = dict(res["batched"]["tuning"])
+        want["first_levels"] = {int(k): v for k, v in want["first_levels"].items()}
+        assert fht.get_batched_tuning() == want
+    fht.set_batched_tuning(None)
+    fht.set_batched_tuning(saved_b)
 
 
 def _model_forward_workspace(h, w, q, levels, acc_u16_ok):
