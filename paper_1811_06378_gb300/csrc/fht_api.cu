@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/fht.h"
 #include "fht_host.h"
 #include "fht_kernels.cuh"
@@ -33,6 +35,12 @@ struct ProfRec {
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
 
+// NVTX ranges per launch (FHT_NVTX=1 when the library loads).
+const bool g_nvtx_on = [] {
+    const char *e = getenv("FHT_NVTX");
+    return e && e[0] == '1' && e[1] == 0;
+}();
+
 cudaEvent_t take_event() {
     if (!g_event_pool.empty()) {
         cudaEvent_t e = g_event_pool.back();
@@ -51,6 +59,10 @@ namespace fht {
 LaunchScope::LaunchScope(const char *name, cudaStream_t st, double alg_bytes)
     : st_(st), bytes_(alg_bytes) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_nvtx_on) {
+        nvtxRangePushA(name);
+        nvtx_ = true;
+    }
     std::lock_guard<std::mutex> lk(g_prof_mu);
     on_ = g_prof_on;
     if (on_) {
@@ -62,6 +74,10 @@ LaunchScope::LaunchScope(const char *name, cudaStream_t st, double alg_bytes)
 }
 
 void LaunchScope::done() {
+    if (nvtx_) {
+        nvtxRangePop();
+        nvtx_ = false;
+    }
     if (!on_) return;
     cudaEventRecord(b_, st_);
     std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -12,7 +12,9 @@ namespace fht {
 
 // Counts a kernel launch and, while profiling is on (fht_profile_begin),
 // brackets it with CUDA events on its stream: construct right before the
-// launch, call done() right after it. alg_bytes: the bytes the launch must
+// launch, call done() right after it. With FHT_NVTX=1 in the environment when
+// the library loads, every launch is also an NVTX range named after the
+// kernel (for nsys / ncu --nvtx filtering); off by default. alg_bytes: the bytes the launch must
 // move at least (the level it reads as stored plus the level it writes).
 class LaunchScope {
   public:
@@ -23,6 +25,7 @@ class LaunchScope {
     cudaStream_t st_;
     double bytes_;
     bool on_ = false;
+    bool nvtx_ = false;   // an NVTX range was pushed for this launch (FHT_NVTX=1)
     std::string name_;
     cudaEvent_t a_ = nullptr, b_ = nullptr;
 };

@@ -86,3 +86,38 @@ def test_final_pass_from_uint16_level_both_forms(staged, tmp_path):
                                    (300, 2500, 3))):
         want = O.quadrant(edges_and_lines(h, w, seed=h + w), q)
         assert (got[f"arr_{i}"] == want.astype(np.int64).astype(np.int32)).all(), (staged, q)
+
+
+CHILD_NVTX = r"""
+import sys
+import numpy as np
+import torch
+import paper_1811_06378_gb300 as fht
+from workloads import edges_and_lines
+img = edges_and_lines(700, 500, seed=5)
+x = torch.from_numpy(img).cuda()
+out = [fht.full_quadrants(x).cpu().numpy(), fht.forward_range(x, 1, 3, 300).cpu().numpy()]
+g = torch.from_numpy(np.random.default_rng(6).standard_normal(fht.full_shape(700, 500))
+                     .astype(np.float32)).cuda()
+out.append(fht.adjoint(g, 700, 500).cpu().numpy())
+out.append(g.cpu().numpy())
+assert fht.device_status() == fht.FHT_OK
+np.savez(sys.argv[1], *out)
+"""
+
+
+def test_nvtx_ranges_leave_results_unchanged(tmp_path):
+    """FHT_NVTX=1 wraps every launch in an NVTX range (for nsys and ncu
+    --nvtx filtering); the results stay the oracle's."""
+    import oracle as O
+    from workloads import edges_and_lines
+    path = str(tmp_path / "out.npz")
+    env = dict(os.environ, FHT_NVTX="1", PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", CHILD_NVTX, path], env=env, cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = np.load(path)
+    img = edges_and_lines(700, 500, seed=5)
+    assert (got["arr_0"] == O.full(img).astype(np.int64).astype(np.int32)).all()
+    assert (got["arr_1"] == O.range_slice(img, 1, 3, 300)).all()
+    assert np.array_equal(got["arr_2"], O.adjoint_full(got["arr_3"], 700, 500, "f32"))
