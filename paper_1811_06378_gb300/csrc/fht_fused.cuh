@@ -281,53 +281,6 @@ __device__ __forceinline__ void reg_butterfly(Acc (&v)[1 << MR][kV]) {
     }
 }
 
-// The same MR levels when only the last level's slopes [tlo, thi] are
-// needed (range pruning): a slope t of level j comes from slope t/2 of level
-// j - 1, so level j computes the pairs u in [lo_j/2, hi_j/2], lo_j = tlo >>
-// (MR - j), hi_j = thi >> (MR - j); the other rows are left as copies (their
-// values are never used). The bounds are warp-uniform.
-template <int MR, typename Acc, int OP = 0>
-__device__ __forceinline__ void reg_butterfly_range(Acc (&v)[1 << MR][kV], int tlo, int thi) {
-    constexpr int R = 1 << MR;
-    int j = 0;
-#pragma unroll
-    for (int half = 1; half < R; half *= 2) {
-        ++j;
-        const int ulo = (tlo >> (MR - j)) >> 1, uhi = (thi >> (MR - j)) >> 1;
-        Acc nv[R][kV];
-#pragma unroll
-        for (int s0 = 0; s0 < R; s0 += 2 * half) {
-#pragma unroll
-            for (int u = 0; u < half; ++u) {
-                const Acc *top = v[s0 + u];
-                const Acc *bot = v[s0 + half + u];
-                if (u < ulo || u > uhi) {
-#pragma unroll
-                    for (int k = 0; k < kV; ++k) {
-                        nv[s0 + 2 * u][k] = top[k];
-                        nv[s0 + 2 * u + 1][k] = top[k];
-                    }
-                    continue;
-                }
-                Acc nb[kV];
-#pragma unroll
-                for (int k = 0; k < kV; ++k) nb[k] = k <= u ? shfl_next(bot[k]) : Acc(0);
-#pragma unroll
-                for (int k = 0; k < kV; ++k) {
-                    Acc b0 = k + u < kV ? bot[k + u] : nb[k + u - kV];
-                    Acc b1 = k + u + 1 < kV ? bot[k + u + 1] : nb[k + u + 1 - kV];
-                    nv[s0 + 2 * u][k] = Combine<Acc, OP>::apply(top[k], b0);
-                    nv[s0 + 2 * u + 1][k] = Combine<Acc, OP>::apply(top[k], b1);
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int k = 0; k < kV; ++k) v[r][k] = nv[r][k];
-    }
-}
-
 // ------------------------------------------------------------ pass geometry
 
 // Tile geometry of a pass with levels MA + MB (host and device agree on it).
@@ -1149,14 +1102,6 @@ __device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &
     constexpr int PAD = TilePad<MidE>::kPad;
     const int P = G.pitch;
     if (ip.black) return;
-    // Level-MA slopes block B reads: its item a2 reads slope a2 of every
-    // mini-strip and runs only if one of the level-k1 slopes
-    // (a << M) + a2*RB .. + RB - 1 is needed (range pruning). A first pass
-    // of a range (every group alike) computes and stores only those.
-    const int base = ip.a << M;
-    const int a2_lo = d.need_lo > base ? (d.need_lo - base) / RB : 0;
-    const int a2_hi = d.need_hi - base >= (RA - 1) * RB ? RA - 1 : (d.need_hi - base) / RB;
-    const bool pruned = a2_lo > 0 || a2_hi < RA - 1;
     // mini-strip g (rows g*RA + rho), warp-column wc
     for (int item = warp; item < RB * G.n_a; item += nwarps) {
         const int g = item % RB, wc = item / RB;
@@ -1164,13 +1109,11 @@ __device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &
         Acc v[RA][kV];
         load_block_a<SG, RA, ADJ, Acc, SrcE, NC>(d, M, ip.S, ip.a, g * RA, ip.A_off,
                                                  wc * kWarpValid, i0, v);
-        if (pruned) reg_butterfly_range<MA, Acc, OP>(v, a2_lo, a2_hi);
-        else reg_butterfly<MA, Acc, OP>(v);
+        reg_butterfly<MA, Acc, OP>(v);
         if (lane < kLanesValid) {
             const int pos = (8 + PAD) * (i0 >> 3);   // i0 is a multiple of 8
 #pragma unroll
             for (int c = 0; c < RA; ++c) {
-                if (c < a2_lo || c > a2_hi) continue;
                 MidE *row = sm + (g * RA + c) * P + pos;
                 if constexpr (PAD == 2) {
                     uint32_t *w = reinterpret_cast<uint32_t *>(row);
