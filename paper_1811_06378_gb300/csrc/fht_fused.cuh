@@ -1129,6 +1129,92 @@ __device__ __forceinline__ void tile_block_a(const PassDesc &d, const TileGeom &
     }
 }
 
+// Transposed image gradient (an adjoint's final pass for Q2/Q3) through
+// shared memory. Block B's item a2 holds, per lane, 8 image rows X (its
+// buffer columns) x RB image columns y (its output rows); stored straight, a
+// warp's 16-byte pieces land in 32 different image rows. Instead, every warp
+// writes its values into the tile region as [xi][y] rows of 2^M floats
+// (xi = X - X_base < T, y - y_base < 2^M), 16-byte granules XOR-swizzled by
+// (xi >> 3) so that neither the writes (lanes 8 rows apart) nor the reads
+// (consecutive granules of a row) conflict; after a CTA barrier the whole
+// CTA adds each image row's 2^M columns as contiguous float4s (old value
+// first, as acc_store does). Used when every warp has exactly one block-B
+// item (the caller checks), RB >= 4 and the tile region holds T x 2^M values.
+template <int M>
+__device__ __forceinline__ int stage_granule(int xi, int gi) {
+    constexpr int G = (1 << M) / 4;   // granules per staged row
+    return xi * G + (gi ^ ((xi >> 3) & (G - 1) & 7));
+}
+
+template <int SG, int M, int RB, typename Acc>
+__device__ __forceinline__ void stage_transposed(float *st, int T, int i0, int yo0,
+                                                 const Acc (&v)[RB][kV]) {
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+        const int xi = SG > 0 ? i0 + k : T - 1 - (i0 + k);
+#pragma unroll
+        for (int h = 0; h < RB / 4; ++h) {
+            const float4 q = make_float4((float)v[4 * h][k], (float)v[4 * h + 1][k],
+                                         (float)v[4 * h + 2][k], (float)v[4 * h + 3][k]);
+            reinterpret_cast<float4 *>(st)[stage_granule<M>(xi, yo0 / 4 + h)] = q;
+        }
+    }
+}
+
+// The CTA's cooperative store of the staged block: image rows X_base + xi
+// (xi < T, X < dst_w... the transposed image's column count is dst_w), image
+// columns y_base .. y_base + 2^M - 1 (< dst_h), added into the gradient when
+// accumulating.
+template <int M, typename DstE>
+__device__ __forceinline__ void store_staged_transposed(const PassDesc &d, const float *st, int T,
+                                                        int X_base, int y_base) {
+    constexpr int G = (1 << M) / 4;
+    constexpr int kB = 4;   // granules per thread whose old values are loaded together
+    DstE *img = reinterpret_cast<DstE *>(d.hi.ptr);
+    const int64_t pitch = d.hi.pitch;
+    const bool vec = (pitch & 3) == 0 && (reinterpret_cast<uintptr_t>(img) & 15) == 0;
+    const int acc = d.accumulate;
+    const int total = T * G, step = blockDim.x;
+    for (int base = threadIdx.x; base < total; base += kB * step) {
+        float4 q[kB], old[kB];
+        DstE *p[kB];
+        int mode[kB];   // 0 nothing, 1 vector, 2 scalar
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            const int idx = base + u * step;
+            mode[u] = 0;
+            p[u] = img;
+            if (idx >= total) continue;
+            const int xi = idx / G, gi = idx - xi * G;
+            const int X = X_base + xi, y = y_base + 4 * gi;
+            if (X < 0 || X >= d.dst_w || y >= d.dst_h) continue;
+            q[u] = reinterpret_cast<const float4 *>(st)[stage_granule<M>(xi, gi)];
+            p[u] = img + (int64_t)X * pitch + y;
+            mode[u] = vec && y + 4 <= d.dst_h ? 1 : 2;
+            if (mode[u] == 1 && acc) old[u] = *reinterpret_cast<const float4 *>(p[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            if (mode[u] == 1) {
+                float4 o = q[u];
+                if (acc) {
+                    o.x = __fadd_rn(old[u].x, q[u].x);
+                    o.y = __fadd_rn(old[u].y, q[u].y);
+                    o.z = __fadd_rn(old[u].z, q[u].z);
+                    o.w = __fadd_rn(old[u].w, q[u].w);
+                }
+                *reinterpret_cast<float4 *>(p[u]) = o;
+            } else if (mode[u] == 2) {
+                const int y0 = (int)((p[u] - img) % pitch);
+                const float e[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (y0 + c < d.dst_h) p[u][c] = acc ? __fadd_rn((float)p[u][c], e[c]) : e[c];
+            }
+        }
+    }
+}
+
 // Block B of a two-block item: level-MA slope a2 of every mini-strip g, read
 // from the shared tile with the shear a2*g, MB more levels, then the
 // destination (zeros for a black tile, without reading the tile).
@@ -1140,6 +1226,45 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
     constexpr int M = MA + MB, RA = 1 << MA, RB = 1 << MB;
     constexpr int PAD = TilePad<MidE>::kPad;
     const int P = G.pitch, T = G.tile_out;
+    // an adjoint's transposed image gradient through the tile region (see
+    // stage_transposed): every warp one item, all items barriered together
+    constexpr bool kStageTr = ADJ && FIN == 2 && RB >= 4 && std::is_same<DstE, float>::value &&
+                              std::is_same<Acc, float>::value;
+    if constexpr (kStageTr) {
+        if (RA * G.n_b == nwarps) {
+            const int a2 = warp;
+            const int slope0 = (ip.a << M) + a2 * RB;
+            const bool run = !(slope0 > d.need_hi || slope0 + RB - 1 < d.need_lo);
+            const int i0 = lane * kV;
+            const int i0r = i0 < T ? i0 : T;
+            Acc v[RB][kV];
+            if (run) {
+#pragma unroll
+                for (int g = 0; g < RB; ++g) {
+                    const int x0 = i0r + a2 * g;
+                    const int delta = x0 & 7;
+                    const MidE *row = sm + (g * RA + a2) * P + tile_pos(x0, PAD);
+                    MidE raw[kV + PAD];
+#pragma unroll
+                    for (int j = 0; j < kV + PAD; ++j) raw[j] = row[j];
+#pragma unroll
+                    for (int k = 0; k < kV; ++k)
+                        v[g][k] = (Acc)(k + delta >= kV ? raw[k + PAD] : raw[k]);
+                }
+                reg_butterfly<MB, Acc, OP>(v);
+            }
+            __syncthreads();   // every warp has read the tile: it becomes the staging area
+            float *st = reinterpret_cast<float *>(const_cast<MidE *>(sm));
+            if (run && lane < kLanesValid && i0 < T)
+                stage_transposed<SG, M, RB, Acc>(st, T, i0, a2 * RB, v);
+            __syncthreads();
+            // buffer column i = 0 is p = D (sign +) or D - (T - 1) (sign -); X = p - sigma_plus*n
+            const int p_lo_tile = SG > 0 ? ip.D : ip.D - (T - 1);
+            const int X_base = p_lo_tile - (SG > 0 ? d.n : 0);
+            store_staged_transposed<M, DstE>(d, st, T, X_base, hi_row(d, M, ip.S, ip.a, 0));
+            return;
+        }
+    }
     for (int item = warp; item < RA * G.n_b; item += nwarps) {
         const int a2 = item % RA, jc = item / RA;
         // level-k1 slopes (a << M) + a2*RB .. + RB - 1 of this item: skip it
