@@ -30,6 +30,8 @@
  *   FHT_ECUDA         a CUDA launch or copy failed (see fht_last_cuda_error)
  *   FHT_EUNSUPPORTED  a valid request this build does not implement
  *   FHT_ETIMEOUT      a device-side bounded wait gave up (batched kernel)
+ *   FHT_EBOUNDS       the debug build refused an access outside a pass's
+ *                     buffers (fht_device_status)
  *
  * Geometry (Section 3.1): for the mostly-vertical quadrants Q0/Q1 the image is
  * zero-padded virtually to n = next_pow2(h) rows and W = w + n columns taken
@@ -64,7 +66,8 @@ typedef enum {
     FHT_ENOMEM = 2,
     FHT_ECUDA = 3,
     FHT_EUNSUPPORTED = 4,
-    FHT_ETIMEOUT = 5
+    FHT_ETIMEOUT = 5,
+    FHT_EBOUNDS = 6
 } fht_status;
 
 typedef enum { FHT_U8 = 0, FHT_I32 = 1, FHT_F32 = 2 } fht_dtype;
@@ -534,14 +537,24 @@ fht_status fht_batched_test_hooks(fht_plan *plan, long long wait_budget_cycles, 
 
 void fht_plan_destroy(fht_plan *plan);
 
-/* Device status of the single-image transforms (fht_forward,
- * fht_forward_range, fht_full_quadrants, fht_adjoint and fht_forward_static).
- * Waits for every launch issued so far in this process, then returns
- * FHT_ETIMEOUT if any kernel recorded a device-side error since the last call
- * (the count is then reset), else FHT_OK; FHT_ECUDA if the device could not
- * be synchronised. The release build's kernels record none, so there the
- * status is FHT_OK whenever the device synchronises. Not in the paper. */
+/* Device status of the transforms' kernels. Waits for every launch issued so
+ * far in this process, then returns FHT_EBOUNDS if a kernel of the debug
+ * build refused an access since the last call (the count is then reset),
+ * else FHT_OK; FHT_ECUDA if the device could not be synchronised. The debug
+ * build (compiled with -DFHT_DEBUG, see below) checks every global load and
+ * store of the pass kernels against the buffers the pass may touch and skips
+ * (a load reads zero) and counts any access outside them; the release
+ * build's kernels check nothing, so there the status is FHT_OK whenever the
+ * device synchronises. Not in the paper. */
 fht_status fht_device_status(void);
+
+/* Test hook of the debug build's bounds checks: every pass launched from now
+ * on records a destination span `shrink_bytes` shorter than its buffer, so
+ * that its last stores are refused (and skipped) and fht_device_status
+ * reports FHT_EBOUNDS; 0 restores the exact spans. Nothing outside the
+ * buffers is ever touched. FHT_EUNSUPPORTED in the release build, FHT_EINVAL
+ * for a negative value. */
+fht_status fht_debug_test_hooks(long long shrink_bytes);
 
 /* ------------------------------------------------------------ tuning
  * How the plain sum transforms and adjoints (fht_forward, fht_forward_range,

@@ -30,15 +30,20 @@ __all__ = [
     "workspace_size_sheared", "shear_range", "forward_sheared",
     "scaled_width", "scaled_shape", "workspace_size_scaled", "scale_range", "forward_scaled",
     "workspace_size_padded", "forward_padded", "merge_strips",
-    "BatchPlan", "FHT_OK", "FHT_ETIMEOUT",
+    "BatchPlan", "FHT_OK", "FHT_ETIMEOUT", "FHT_EBOUNDS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libfht.so")
+# FHT_DEBUG=1 loads the bounds-checked build (python -m
+# paper_1811_06378_gb300.build --debug): every global access of the pass
+# kernels is checked against the pass's buffers; device_status() reports
+# FHT_EBOUNDS for any refused access.
+DEBUG = os.environ.get("FHT_DEBUG") == "1"
+LIB_PATH = os.path.join(_HERE, "_build", "debug" if DEBUG else "", "libfht.so")
 
 Q0, Q1, Q2, Q3 = 0, 1, 2, 3
 LAYOUT_QUADRANT, LAYOUT_FULL = 0, 1
-FHT_OK, FHT_ETIMEOUT = 0, 5
+FHT_OK, FHT_ETIMEOUT, FHT_EBOUNDS = 0, 5, 6
 _U8, _I32, _F32 = 0, 1, 2
 _DTYPE = {torch.uint8: _U8, torch.int32: _I32, torch.float32: _F32}
 
@@ -62,9 +67,9 @@ class BatchedTuning(ctypes.Structure):
 
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
-        raise ImportError(
-            f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; "
-            "g.build()'` (needs nvcc for sm_103a)")
+        how = ("python -m paper_1811_06378_gb300.build --debug" if DEBUG else
+               "python -c 'import __graft_entry__ as g; g.build()'")
+        raise ImportError(f"{LIB_PATH} is not built; run `{how}` (needs nvcc for sm_103a)")
     L = ctypes.CDLL(LIB_PATH)
     vp, i, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
     ip = ctypes.POINTER(ctypes.c_int)
@@ -107,6 +112,7 @@ def _load() -> ctypes.CDLL:
         "fht_profile_end": (i, [vp, i, ip]),
         "fht_launch_count": (ctypes.c_longlong, []),
         "fht_device_status": (ctypes.c_int, []),
+        "fht_debug_test_hooks": (ctypes.c_int, [ctypes.c_longlong]),
         "fht_workspace_size_many": (i, [i, i, i, i, i, ctypes.POINTER(sz)]),
         "fht_forward_many": (i, [vp, i, i64, i, i, i64, i, i, vp, i64, i64, vp, sz, vp]),
         "fht_adjoint_many": (i, [vp, i, i64, i, i, i, i, i64, vp, i64, i64, vp, sz, vp]),
@@ -738,8 +744,9 @@ def launch_count() -> int:
 
 
 def device_status() -> int:
-    """Wait for the device; FHT_ETIMEOUT if a kernel recorded a device-side
-    error since the last call (the count is reset), else FHT_OK."""
+    """Wait for the device; FHT_EBOUNDS if a kernel of the debug build
+    refused an access outside its pass's buffers since the last call (the
+    count is reset), else FHT_OK."""
     return int(lib.fht_device_status())
 
 

@@ -2,6 +2,8 @@
 
 Every csrc/*.cu is one translation unit; they compile in parallel and link
 into paper_1811_06378_gb300/_build/libfht.so (CUDA runtime linked statically).
+`--debug` builds the bounds-checked variant (-DFHT_DEBUG) into
+_build/debug/libfht.so; the package loads it when FHT_DEBUG=1.
 """
 
 from __future__ import annotations
@@ -18,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 OBJ = os.path.join(BUILD, "obj")
 LIB = os.path.join(BUILD, "libfht.so")
+DEBUG_BUILD = os.path.join(BUILD, "debug")
+DEBUG_LIB = os.path.join(DEBUG_BUILD, "libfht.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,10 +35,10 @@ def _headers() -> list[str]:
             + [os.path.join(ROOT, "include", "fht.h")])
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, verbose: bool, obj_dir: str = OBJ, defines=()) -> str:
+    obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj + ".tmp"]
+           *defines, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     subprocess.check_call(cmd)
@@ -42,26 +46,30 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    obj_dir = os.path.join(DEBUG_BUILD, "obj") if debug else OBJ
+    lib = DEBUG_LIB if debug else LIB
+    defines = ("-DFHT_DEBUG",) if debug else ()
+    os.makedirs(obj_dir, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     newest_header = max(os.path.getmtime(h) for h in _headers())
     todo = []
     for src in sources:
-        obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(
                 os.path.getmtime(src), newest_header):
             todo.append(src)
     if todo:
         with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
-            list(ex.map(lambda s: _compile(s, verbose), todo))
-    objs = [os.path.join(OBJ, os.path.basename(s)[:-3] + ".o") for s in sources]
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + f".{os.getpid()}.tmp"
+            list(ex.map(lambda s: _compile(s, verbose, obj_dir, defines), todo))
+    objs = [os.path.join(obj_dir, os.path.basename(s)[:-3] + ".o") for s in sources]
+    if todo or not os.path.exists(lib):
+        tmp = lib + f".{os.getpid()}.tmp"
         subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                debug="--debug" in sys.argv))

@@ -35,6 +35,9 @@ struct ProfRec {
 std::vector<ProfRec> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
 
+// Bytes taken off every destination span (fht_debug_test_hooks).
+std::atomic<long long> g_debug_shrink{0};
+
 // NVTX ranges per launch (FHT_NVTX=1 when the library loads).
 const bool g_nvtx_on = [] {
     const char *e = getenv("FHT_NVTX");
@@ -330,6 +333,8 @@ std::vector<unsigned int (*)()> &counter_fns() {
 namespace fht {
 
 bool staged_enabled() { return g_tune.staged; }
+
+long long debug_hi_shrink() { return g_debug_shrink.load(); }
 
 bool register_device_counter(unsigned int (*read_and_reset)()) {
     std::lock_guard<std::mutex> lk(counter_mu());
@@ -677,6 +682,7 @@ const char *fht_status_string(fht_status s) {
     case FHT_ECUDA: return "CUDA error";
     case FHT_EUNSUPPORTED: return "unsupported";
     case FHT_ETIMEOUT: return "device wait timed out";
+    case FHT_EBOUNDS: return "access outside a pass's buffers (debug build)";
     }
     return "unknown status";
 }
@@ -1415,7 +1421,18 @@ fht_status fht_device_status(void) {
         g_last_cuda_error = (int)cudaGetLastError();
         return FHT_ECUDA;
     }
-    return read_device_counters() ? FHT_ETIMEOUT : FHT_OK;
+    return read_device_counters() ? FHT_EBOUNDS : FHT_OK;
+}
+
+fht_status fht_debug_test_hooks(long long shrink_bytes) {
+#ifdef FHT_DEBUG
+    if (shrink_bytes < 0) return FHT_EINVAL;
+    g_debug_shrink.store(shrink_bytes);
+    return FHT_OK;
+#else
+    (void)shrink_bytes;
+    return FHT_EUNSUPPORTED;
+#endif
 }
 
 fht_status fht_profile_begin(void) {

@@ -388,6 +388,7 @@ fht_status launch_table(fht_plan *plan, Table &T, const CallPtrs *calls, Kernel 
         } else {
             sg.d.hi.ptr = ws + sg.hi_off;
         }
+        set_debug_extents(sg.d);
     }
     cudaError_t e = cudaMemcpyAsync(ws, table, T.counters_off, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !capturing) {

@@ -101,6 +101,9 @@ struct PassDesc {
     // transform (fht_forward_range, fht_forward_op with a slope range), whose
     // launches are named apart from those of whole quadrants.
     int range_call;
+    // Bytes from lo.ptr / hi.ptr the pass may touch (0: unknown); read only by
+    // the debug build's bounds checks (fht_debug.cuh).
+    long long dbg_lo_bytes, dbg_hi_bytes;
 };
 
 __host__ __device__ inline int64_t floor_mod(int64_t v, int64_t m) {

@@ -24,6 +24,7 @@
 
 #include <type_traits>
 
+#include "fht_debug.cuh"
 #include "fht_kernels.cuh"
 
 namespace fht {
@@ -82,7 +83,7 @@ __device__ __noinline__ Vec8<Acc> load8_edge(const E *row, int lo, int cols) {
 #pragma unroll
     for (int k = 0; k < kV; ++k) {
         const int c = lo + k;
-        r.x[k] = (c >= 0 && c < cols) ? (Acc)row[c] : Acc(0);
+        r.x[k] = (c >= 0 && c < cols && FHT_LOAD_OK(row + c, sizeof(E))) ? (Acc)row[c] : Acc(0);
     }
     return r;
 }
@@ -92,7 +93,7 @@ __device__ __noinline__ void store8_edge(E *row, int lo, int cols, Vec8<Acc> v) 
 #pragma unroll
     for (int k = 0; k < kV; ++k) {
         const int c = lo + k;
-        if (c >= 0 && c < cols) row[c] = (E)v.x[k];
+        if (c >= 0 && c < cols && FHT_STORE_OK(row + c, sizeof(E))) row[c] = (E)v.x[k];
     }
 }
 
@@ -116,6 +117,11 @@ __device__ __forceinline__ V ldvec(const V *p) {
 // so the loads of several rows can all be in flight together).
 template <typename E, typename Acc, bool NC = true>
 __device__ __forceinline__ void load8_fast(const E *row, int lo, Acc (&v)[kV]) {
+    if (!FHT_LOAD_OK(row + lo, kV * sizeof(E))) {
+#pragma unroll
+        for (int k = 0; k < kV; ++k) v[k] = Acc(0);
+        return;
+    }
     const uintptr_t a = reinterpret_cast<uintptr_t>(row + lo);
     if constexpr (sizeof(E) == 1) {
         const int delta = (int)(a & 7);
@@ -194,7 +200,7 @@ __device__ __forceinline__ void load8_cyclic(const E *row, int lo, int W, Acc (&
         int x = c + k;
         if (x >= W) x -= W;
         if (x >= W) x %= W;
-        v[k] = (Acc)row[x];
+        v[k] = FHT_LOAD_OK(row + x, sizeof(E)) ? (Acc)row[x] : Acc(0);
     }
 }
 
@@ -216,6 +222,7 @@ template <typename E, typename Acc, bool kStream = false>
 __device__ __forceinline__ void store8(E *row, int lo, int cols, const Acc (&v)[kV]) {
     E *p = row + lo;
     if (lo >= 0 && lo + kV <= cols && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        if (!FHT_STORE_OK(p, kV * sizeof(E))) return;
         if constexpr (sizeof(E) == 2) {
             uint4 q;
             q.x = pack_u16x2((uint32_t)v[0], (uint32_t)v[1]);
@@ -424,9 +431,9 @@ __device__ __noinline__ Vec8<Acc> load8_sheared_edge(const PassDesc &d, const Sr
         int c = c0 + k;
         if (c >= d.W) c -= d.W;
         Acc v = Acc(0);
-        if (c < d.lo.cols)
-            v = d.transpose ? (Acc)img[(int64_t)c * d.lo.pitch + y]
-                            : (Acc)img[(int64_t)y * d.lo.pitch + c];
+        const SrcE *q = d.transpose ? img + (int64_t)c * d.lo.pitch + y
+                                    : img + (int64_t)y * d.lo.pitch + c;
+        if (c < d.lo.cols && FHT_LOAD_OK(q, sizeof(SrcE))) v = (Acc)*q;
         r.x[k] = v;
     }
     return r;
@@ -480,6 +487,7 @@ __device__ __forceinline__ void load_block_a_sheared(const PassDesc &d, int row0
 // Scalar load; NC as in ldvec.
 template <bool NC, typename T>
 __device__ __forceinline__ T ldscalar(const T *p) {
+    if (!FHT_LOAD_OK(p, sizeof(T))) return T(0);
     if constexpr (NC) return __ldg(p);
     else return *p;
 }
@@ -702,7 +710,7 @@ __device__ __noinline__ void store_final_edge(const PassDesc &d, DstE *row, int 
         if (p >= 0 && p < W) {
             int X = p + off;
             if (X >= W) X -= W;
-            row[X] = (DstE)v.x[k];
+            if (FHT_STORE_OK(row + X, sizeof(DstE))) row[X] = (DstE)v.x[k];
         }
     }
 }
@@ -760,7 +768,7 @@ __device__ __noinline__ void store_win_edge(DstE *row, int lo, int b, int W, int
         if (x >= W) continue;
         int j = x - b;
         if (j < 0) j += W;
-        if (j < L) row[j] = (DstE)v.x[k];
+        if (j < L && FHT_STORE_OK(row + j, sizeof(DstE))) row[j] = (DstE)v.x[k];
     }
 }
 
@@ -834,7 +842,8 @@ __device__ __noinline__ void store_image_row_edge(DstE *row, int X0, int lo, int
 #pragma unroll
     for (int k = 0; k < kV; ++k) {
         const int p = lo + k;
-        if (p >= p_lo && p < p_hi) row[X0 + k] = acc_store<DstE, Acc>(row[X0 + k], a.x[k], acc);
+        if (p >= p_lo && p < p_hi && FHT_STORE_OK(row + X0 + k, sizeof(DstE)))
+            row[X0 + k] = acc_store<DstE, Acc>(row[X0 + k], a.x[k], acc);
     }
 }
 
@@ -845,7 +854,8 @@ __device__ __noinline__ void store_image_col_edge(DstE *row, int y0, int dst_h, 
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int y = y0 + r;
-        if (y < dst_h) row[y] = acc_store<DstE, Acc>(row[y], col.x[r], acc);
+        if (y < dst_h && FHT_STORE_OK(row + y, sizeof(DstE)))
+            row[y] = acc_store<DstE, Acc>(row[y], col.x[r], acc);
     }
 }
 
@@ -880,6 +890,7 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     if (r >= rows || r < r_lo) continue;
+                    if (!FHT_STORE_OK(base + r * pitch, kV * sizeof(DstE))) continue;
                     V4 a, b;
                     a.x = (DstE)v[r][sg > 0 ? 0 : 7];
                     a.y = (DstE)v[r][sg > 0 ? 1 : 6];
@@ -901,7 +912,8 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
                 V4 old[B][2];
 #pragma unroll
                 for (int j = 0; j < B; ++j) {
-                    if (r0 + j < rows && r0 + j >= r_lo) {
+                    if (r0 + j < rows && r0 + j >= r_lo &&
+                        FHT_STORE_OK(base + (r0 + j) * pitch, kV * sizeof(DstE))) {
                         const V4 *q = reinterpret_cast<const V4 *>(base + (r0 + j) * pitch);
                         old[j][0] = q[0];
                         old[j][1] = q[1];
@@ -911,6 +923,7 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
                 for (int j = 0; j < B; ++j) {
                     const int r = r0 + j;
                     if (r >= rows || r < r_lo) continue;
+                    if (!FHT_STORE_OK(base + r * pitch, kV * sizeof(DstE))) continue;
                     Acc asc[kV];
 #pragma unroll
                     for (int k = 0; k < kV; ++k) asc[k] = sg > 0 ? v[r][k] : v[r][kV - 1 - k];
@@ -954,6 +967,7 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
                 for (int k = 0; k < kV; ++k) {
                     const int kk = sg > 0 ? k : kV - 1 - k;
                     V4 *q = reinterpret_cast<V4 *>(img + (int64_t)(X0 + k) * pitch + y0);
+                    if (!FHT_STORE_OK(q, NV * sizeof(V4))) continue;
 #pragma unroll
                     for (int u = 0; u < NV; ++u) {
                         V4 o;
@@ -973,13 +987,17 @@ __device__ __forceinline__ void store_image_block(const PassDesc &d, int y0, int
                 for (int j = 0; j < kB; ++j)
 #pragma unroll
                     for (int u = 0; u < NV; ++u)
-                        old[j][u] = reinterpret_cast<const V4 *>(
-                            img + (int64_t)(X0 + k0 + j) * pitch + y0)[u];
+                        old[j][u] = FHT_LOAD_OK(img + (int64_t)(X0 + k0 + j) * pitch + y0,
+                                                NV * sizeof(V4))
+                                        ? reinterpret_cast<const V4 *>(
+                                              img + (int64_t)(X0 + k0 + j) * pitch + y0)[u]
+                                        : V4{};
 #pragma unroll
                 for (int j = 0; j < kB; ++j) {
                     const int k = k0 + j;
                     const int kk = sg > 0 ? k : kV - 1 - k;
                     V4 *q = reinterpret_cast<V4 *>(img + (int64_t)(X0 + k) * pitch + y0);
+                    if (!FHT_STORE_OK(q, NV * sizeof(V4))) continue;
 #pragma unroll
                     for (int u = 0; u < NV; ++u) {
                         V4 o = old[j][u];
@@ -1191,6 +1209,7 @@ __device__ __forceinline__ void store_staged_transposed(const PassDesc &d, const
             q[u] = reinterpret_cast<const float4 *>(st)[stage_granule<M>(xi, gi)];
             p[u] = img + (int64_t)X * pitch + y;
             mode[u] = vec && y + 4 <= d.dst_h ? 1 : 2;
+            if (mode[u] == 1 && !FHT_STORE_OK(p[u], sizeof(float4))) mode[u] = 0;
             if (mode[u] == 1 && acc) old[u] = *reinterpret_cast<const float4 *>(p[u]);
         }
 #pragma unroll
@@ -1209,7 +1228,8 @@ __device__ __forceinline__ void store_staged_transposed(const PassDesc &d, const
                 const float e[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    if (y0 + c < d.dst_h) p[u][c] = acc ? __fadd_rn((float)p[u][c], e[c]) : e[c];
+                    if (y0 + c < d.dst_h && FHT_STORE_OK(p[u] + c, sizeof(DstE)))
+                        p[u][c] = acc ? __fadd_rn((float)p[u][c], e[c]) : e[c];
             }
         }
     }
@@ -1337,6 +1357,7 @@ template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename SrcE
 __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm) {
     constexpr int M = MA + MB, RA = 1 << MA;
     constexpr int PAD = TilePad<MidE>::kPad;
+    FHT_DEBUG_BEGIN(d);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const TileGeom G = tile_geom(MA, MB, d.n_a, nwarps, PAD);

@@ -138,6 +138,7 @@ void (*fused_kernel_ptr(int sigma))(PassDesc) {
 // (fht_staged.cuh): grid = SMs x resident CTAs, items taken in turn.
 template <typename Dummy = void>
 cudaError_t launch_staged(PassDesc d, cudaStream_t st) {
+    set_debug_extents(d);
     const TileGeom G = tile_geom(3, 3, 1, 8, 1);
     const int tile_bytes = (1 << 6) * G.pitch * (int)sizeof(int32_t);
     const size_t smem = (size_t)tile_bytes + 8 * kStageWarpElems * sizeof(uint16_t);
@@ -172,6 +173,7 @@ template <int MA, int MB, bool ADJ, typename Acc, typename SrcE, typename MidE, 
 cudaError_t launch_fused_t(PassDesc d, cudaStream_t st) {
     static_assert(OP == 0 || !ADJ, "max / min transforms have no adjoint");
     if (d.batch < 1 || d.batch > 65535) return cudaErrorInvalidValue;
+    set_debug_extents(d);
     if constexpr (!kBatchable<Acc, SrcE> || OP != 0) {
         if (d.batch > 1) return cudaErrorNotSupported;
     }

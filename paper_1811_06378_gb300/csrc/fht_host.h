@@ -41,6 +41,49 @@ unsigned int read_device_counters();
 // kernel (fht_staged.cuh; FHT_STAGED=0 in the environment turns it off).
 bool staged_enabled();
 
+// Bytes the debug build's test hook takes off every destination span
+// (fht_debug_test_hooks; 0 normally).
+long long debug_hi_shrink();
+
+inline size_t elem_size(int type) { return type == kU8 ? 1 : type == kU16 ? 2 : 4; }
+
+// The spans a pass may touch (PassDesc::dbg_lo_bytes / dbg_hi_bytes), from
+// the descriptor's own geometry: a level buffer is n rows of its pitch; the
+// caller's image is its rows x columns view (transposed for Q2/Q3, the
+// unscaled width for the scaled transform); a gradient source covers the
+// rows its row map reaches; a destination covers the rows and columns its
+// map writes. Only the debug build reads them.
+inline void set_debug_extents(PassDesc &d) {
+    const long long le = (long long)elem_size(d.lo.type), he = (long long)elem_size(d.hi.type);
+    long long lo = 0, hi = 0;
+    if (!d.lo_image) {
+        lo = (long long)d.n * d.lo.pitch * le;
+    } else if (d.cyclic && !d.shear_on) {
+        const long long r0 = d.src_row_base + (long long)d.src_row_dir * d.src_t_first;
+        const long long r1 = d.src_row_base + (long long)d.src_row_dir * d.src_t_last;
+        lo = ((r0 > r1 ? r0 : r1) * d.lo.pitch + d.W) * le;
+    } else {
+        long long cols = d.lo.cols;
+        if (d.scale_step) cols = (((long long)d.lo.cols - 1) * d.scale_step >> 32) + 1;
+        const long long mr = d.transpose ? cols : d.lo.rows, mc = d.transpose ? d.lo.rows : cols;
+        lo = ((mr - 1) * d.lo.pitch + mc) * le;
+    }
+    if (!d.hi_final) {
+        hi = (long long)d.n * d.hi.pitch * he;
+    } else if (d.dst_image) {
+        const long long rows = d.dst_transpose ? d.dst_w : d.dst_h - d.dst_row_lo;
+        const long long cols = d.dst_transpose ? d.dst_h : d.dst_w;
+        hi = ((rows - 1) * d.hi.pitch + cols) * he;
+    } else {
+        const long long r0 = d.row_base + (long long)d.row_dir * d.t_first;
+        const long long r1 = d.row_base + (long long)d.row_dir * d.t_last;
+        hi = ((r0 > r1 ? r0 : r1) * d.hi.pitch + d.W) * he;
+    }
+    d.dbg_lo_bytes = lo > 0 ? lo : 0;
+    hi -= debug_hi_shrink();
+    d.dbg_hi_bytes = hi > 0 ? hi : 0;
+}
+
 // Window of the level an adjoint's final pass reads (final pass of Mf levels,
 // cropped to the w_c columns p in [p_begin, p_begin + w_c), p_begin = n for
 // sign +1 and 0 for sign -1): row (s, a) is read on the w_c + 2^Mf - 1

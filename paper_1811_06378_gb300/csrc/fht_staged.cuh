@@ -62,6 +62,7 @@ __device__ __forceinline__ void stage_rows(const PassDesc &d, const ItemPos &ip,
         int bytes = 0;
         if (c >= 0 && c < d.lo.cols) bytes = d.lo.cols - c >= 8 ? 16 : 2 * (d.lo.cols - c);
         const uint16_t *src = base + row * d.lo.pitch + (bytes > 0 ? c : 0);
+        if (bytes > 0 && !FHT_LOAD_OK(src, bytes)) bytes = 0;
         cp_async16(stage + rho * kStageRowElems + 8 * k, src, bytes);
     }
     cp_async_commit();
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(8 * 32, 2)
     int32_t *tile = reinterpret_cast<int32_t *>(smem_raw);
     uint16_t *stage = reinterpret_cast<uint16_t *>(smem_raw + tile_bytes) + warp * kStageWarpElems;
     const int tiles = d.tiles;
+    FHT_DEBUG_BEGIN(d);
     int item = blockIdx.x;
     ItemPos ip{};
     if (item < n_items) {

@@ -297,3 +297,12 @@ def test_segment_bad_arguments(fht):
                             ctypes.c_void_p(0x1000), ctypes.c_void_p(0)) == EINVAL  # u8
     assert L.fht_row_argmax(ctypes.c_void_p(0x1000), 1, 4, 4, 3, ctypes.c_void_p(0x1000),
                             ctypes.c_void_p(0x1000), ctypes.c_void_p(0)) == EINVAL  # pitch
+
+
+def test_debug_hook_is_debug_build_only(fht):
+    """The release build compiles no bounds checks: its test hook reports
+    FHT_EUNSUPPORTED, and FHT_EBOUNDS has a name."""
+    if fht.DEBUG:
+        pytest.skip("the debug build is loaded")
+    assert fht.lib.fht_debug_test_hooks(0) == 4
+    assert b"debug build" in fht.lib.fht_status_string(6)
