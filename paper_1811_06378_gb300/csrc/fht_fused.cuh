@@ -171,6 +171,41 @@ __device__ __forceinline__ void load8_fast(const E *row, int lo, Acc (&v)[kV]) {
     }
 }
 
+// v[k] = p[k] for k < 8, p on a vector granule (8 bytes for uint8, 16
+// otherwise) and all 8 in bounds: whole vectors, no realignment.
+template <typename E, typename Acc, bool NC = true>
+__device__ __forceinline__ void load8_aligned(const E *p, Acc (&v)[kV]) {
+    if (!FHT_LOAD_OK(p, kV * sizeof(E))) {
+#pragma unroll
+        for (int k = 0; k < kV; ++k) v[k] = Acc(0);
+        return;
+    }
+    if constexpr (sizeof(E) == 1) {
+        const uint2 q = ldvec<NC>(reinterpret_cast<const uint2 *>(p));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (Acc)(int32_t)__byte_perm(q.x, 0u, 0x4440u | k);
+            v[k + 4] = (Acc)(int32_t)__byte_perm(q.y, 0u, 0x4440u | k);
+        }
+    } else if constexpr (sizeof(E) == 2) {
+        const uint4 q = ldvec<NC>(reinterpret_cast<const uint4 *>(p));
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            v[2 * i] = (Acc)(int32_t)(w[i] & 0xffffu);
+            v[2 * i + 1] = (Acc)(int32_t)(w[i] >> 16);
+        }
+    } else {
+        const uint4 q0 = ldvec<NC>(reinterpret_cast<const uint4 *>(p));
+        const uint4 q1 = ldvec<NC>(reinterpret_cast<const uint4 *>(p) + 1);
+        const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        using IsF = std::integral_constant<bool, std::is_same<Acc, float>::value &&
+                                                     std::is_same<E, float>::value>;
+#pragma unroll
+        for (int k = 0; k < kV; ++k) v[k] = from_word<Acc>(w[k], IsF());
+    }
+}
+
 // v[k] = row[lo + k] for k < 8, zero outside [0, cols).
 template <typename E, typename Acc, bool NC = true>
 __device__ __forceinline__ void load8(const E *row, int lo, int cols, Acc (&v)[kV]) {
@@ -249,6 +284,34 @@ __device__ __forceinline__ void store8(E *row, int lo, int cols, const Acc (&v)[
 #pragma unroll
         for (int k = 0; k < kV; ++k) r.x[k] = v[k];
         store8_edge<E, Acc>(row, lo, cols, r);
+    }
+}
+
+// 8 ascending elements to p[0..7], p 16-byte aligned and the 8 columns in
+// bounds (the caller checked both once for all its rows).
+template <typename E, typename Acc, bool kStream = false>
+__device__ __forceinline__ void store8_vec(E *p, const Acc (&v)[kV]) {
+    if (!FHT_STORE_OK(p, kV * sizeof(E))) return;
+    if constexpr (sizeof(E) == 2) {
+        uint4 q;
+        q.x = pack_u16x2((uint32_t)v[0], (uint32_t)v[1]);
+        q.y = pack_u16x2((uint32_t)v[2], (uint32_t)v[3]);
+        q.z = pack_u16x2((uint32_t)v[4], (uint32_t)v[5]);
+        q.w = pack_u16x2((uint32_t)v[6], (uint32_t)v[7]);
+        if constexpr (kStream) __stcs(reinterpret_cast<uint4 *>(p), q);
+        else *reinterpret_cast<uint4 *>(p) = q;
+    } else {
+        using V4 = typename std::conditional<std::is_same<E, float>::value, float4, int4>::type;
+        V4 a, b;
+        a.x = (E)v[0]; a.y = (E)v[1]; a.z = (E)v[2]; a.w = (E)v[3];
+        b.x = (E)v[4]; b.y = (E)v[5]; b.z = (E)v[6]; b.w = (E)v[7];
+        if constexpr (kStream) {
+            __stcs(reinterpret_cast<V4 *>(p), a);
+            __stcs(reinterpret_cast<V4 *>(p) + 1, b);
+        } else {
+            reinterpret_cast<V4 *>(p)[0] = a;
+            reinterpret_cast<V4 *>(p)[1] = b;
+        }
     }
 }
 
@@ -654,6 +717,26 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
         }
     }
     const SrcE *p0 = base + first_row * d.lo.pitch;
+    // Rows that are not sheared against each other (an image's rows) and
+    // start on a vector granule, with a row stride of whole granules (a first
+    // pass over an aligned image: tiles start on multiples of 8 columns):
+    // whole vectors, no realignment. The same for every lane (lanes are 8
+    // columns apart), so the branch is warp-uniform.
+    // Not compiled for uint16 sources: those are always sheared intermediate
+    // levels, whose kernels would only carry the extra code.
+    if constexpr (sizeof(SrcE) != 2) {
+        constexpr uintptr_t kGran = sizeof(SrcE) == 1 ? 8 : 16;
+        if (dlo == 0 && ((reinterpret_cast<uintptr_t>(p0 + lo0) |
+                          (uintptr_t)(stride * (int64_t)sizeof(SrcE))) & (kGran - 1)) == 0) {
+            const SrcE *p = p0 + lo0;
+#pragma unroll
+            for (int r = 0; r < RA; ++r) {
+                load8_aligned<SrcE, Acc, NC>(p + r * stride, v[r]);
+                if constexpr (sg < 0) reverse8(v[r]);
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int r = 0; r < RA; ++r) {
         load8_fast<SrcE, Acc, NC>(p0 + r * stride, lo0 + r * dlo, v[r]);
@@ -725,13 +808,23 @@ __device__ __forceinline__ void store_rows(const PassDesc &d, const DestCols &c,
     if constexpr (!FIN) {
         DstE *row = base + (int64_t)hi_r0 * d.hi.pitch;
         const int64_t stride = d.hi.pitch;
+        if (c.vec) {   // aligned and in bounds for every row: no per-row checks
+            DstE *p = row + c.lo;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                Acc asc[kV];
+#pragma unroll
+                for (int k = 0; k < kV; ++k) asc[k] = SG > 0 ? v[r][k] : v[r][kV - 1 - k];
+                store8_vec<DstE, Acc>(p + r * stride, asc);
+            }
+            return;
+        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             Acc asc[kV];
 #pragma unroll
             for (int k = 0; k < kV; ++k) asc[k] = SG > 0 ? v[r][k] : v[r][kV - 1 - k];
-            if (c.vec) store8<DstE, Acc>(row + r * stride, c.lo, c.lo + kV, asc);
-            else store8<DstE, Acc>(row + r * stride, c.lo, d.hi.cols, asc);
+            store8<DstE, Acc>(row + r * stride, c.lo, d.hi.cols, asc);
         }
         return;
     } else {
@@ -739,15 +832,25 @@ __device__ __forceinline__ void store_rows(const PassDesc &d, const DestCols &c,
     const int r_lo = d.t_first - t0, r_hi = d.t_last - t0;   // rows r in [r_lo, r_hi] exist
     DstE *row = base + ((int64_t)d.row_base + (int64_t)d.row_dir * t0) * d.hi.pitch;
     const int64_t stride = (int64_t)d.row_dir * d.hi.pitch;
+    if (c.vec) {   // aligned and in bounds for every row: no per-row checks
+        DstE *p = row + c.X0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r < r_lo || r > r_hi) continue;
+            Acc asc[kV];
+#pragma unroll
+            for (int k = 0; k < kV; ++k) asc[k] = SG > 0 ? v[r][k] : v[r][kV - 1 - k];
+            store8_vec<DstE, Acc, true>(p + r * stride, asc);
+        }
+        return;
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (r < r_lo || r > r_hi) continue;
         Acc asc[kV];
 #pragma unroll
         for (int k = 0; k < kV; ++k) asc[k] = SG > 0 ? v[r][k] : v[r][kV - 1 - k];
-        if (c.vec) {
-            store8<DstE, Acc, true>(row + r * stride, c.X0, c.X0 + kV, asc);
-        } else {
+        {
             Vec8<Acc> e;
 #pragma unroll
             for (int k = 0; k < kV; ++k) e.x[k] = asc[k];
