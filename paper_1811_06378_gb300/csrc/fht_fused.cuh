@@ -351,6 +351,12 @@ __device__ __forceinline__ void reg_butterfly(Acc (&v)[1 << MR][kV]) {
     }
 }
 
+}  // namespace fht
+
+#include "fht_packed.cuh"
+
+namespace fht {
+
 // ------------------------------------------------------------ pass geometry
 
 // Tile geometry of a pass with levels MA + MB (host and device agree on it).
@@ -1445,6 +1451,160 @@ __device__ __forceinline__ void tile_block_b(const PassDesc &d, const TileGeom &
     }
 }
 
+// ------------------------------------------------------------ packed first pass
+
+// Block A's RA rows of a uint8 image as packed words in buffer order: an
+// aligned interior item reads one 8-byte vector per row and packs its bytes
+// straight into 16-bit halves; every other case (image edges, unaligned rows,
+// the transposed load) takes the general loader and packs its values.
+template <int SG, int RA>
+__device__ __forceinline__ void load_block_a_u8x2(const PassDesc &d, int M, int S, int s0,
+                                                  int A_off, int wbase, int i0,
+                                                  uint32_t (&w)[RA][4]) {
+    constexpr int sg = SG;
+    const int splus = sg > 0 ? 1 : 0;
+    if (!d.transpose) {
+        const int lo_min = sg > 0 ? A_off + wbase : A_off - wbase - (32 * kV - 1);
+        const int hi_max = sg > 0 ? A_off + wbase + 32 * kV : A_off - wbase + 1;
+        const int row0 = S * (1 << M) + s0;
+        const int p_first = A_off + sg * i0;
+        const int lo0 = (sg > 0 ? p_first : p_first - (kV - 1)) - splus;
+        const uint8_t *p = reinterpret_cast<const uint8_t *>(d.lo.ptr) + (int64_t)row0 * d.lo.pitch + lo0;
+        if (lo_min - splus >= 0 && hi_max - splus <= d.lo.cols && row0 + RA <= d.lo.rows &&
+            ((reinterpret_cast<uintptr_t>(p) | (uintptr_t)d.lo.pitch) & 7) == 0) {
+#pragma unroll
+            for (int r = 0; r < RA; ++r) {
+                const uint8_t *q8 = p + (int64_t)r * d.lo.pitch;
+                uint2 q = make_uint2(0u, 0u);
+                if (FHT_LOAD_OK(q8, 8)) q = ldvec<true>(reinterpret_cast<const uint2 *>(q8));
+                if constexpr (sg > 0) {
+                    w[r][0] = __byte_perm(q.x, 0u, 0x4140u);
+                    w[r][1] = __byte_perm(q.x, 0u, 0x4342u);
+                    w[r][2] = __byte_perm(q.y, 0u, 0x4140u);
+                    w[r][3] = __byte_perm(q.y, 0u, 0x4342u);
+                } else {   // buffer order runs down the image columns
+                    w[r][0] = __byte_perm(q.y, 0u, 0x4243u);
+                    w[r][1] = __byte_perm(q.y, 0u, 0x4041u);
+                    w[r][2] = __byte_perm(q.x, 0u, 0x4243u);
+                    w[r][3] = __byte_perm(q.x, 0u, 0x4041u);
+                }
+            }
+            return;
+        }
+    }
+    int32_t v[RA][kV];
+    load_block_a<SG, RA, false, int32_t, uint8_t>(d, M, S, 0, s0, A_off, wbase, i0, v);
+#pragma unroll
+    for (int r = 0; r < RA; ++r)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[r][j] = pack_u16x2((uint32_t)v[r][2 * j], (uint32_t)v[r][2 * j + 1]);
+}
+
+// Word j of 8 buffer columns from x0 of a uint16 tile row (the two 8-column
+// groups around x0, with the pad word between them skipped).
+__device__ __forceinline__ void tile_read_u16x2(const uint16_t *row_group, int delta,
+                                                uint32_t (&w)[4]) {
+    const uint32_t *g = reinterpret_cast<const uint32_t *>(row_group);
+    // words of the two groups without the pad: e[0..3] group A, e[4..7] group B
+    uint32_t e[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        e[i] = g[i];
+        e[4 + i] = g[5 + i];
+    }
+    const int m = delta >> 1;
+    uint32_t u[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        u[i] = sel4(e[i], e[i + 1 < 8 ? i + 1 : 7], e[i + 2 < 8 ? i + 2 : 7],
+                    e[i + 3 < 8 ? i + 3 : 7], m);
+    if (delta & 1) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[j] = __byte_perm(u[j], u[j + 1], 0x5432u);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w[j] = u[j];
+    }
+}
+
+// The two-block first pass of a sum transform from a uint8 image into a
+// uint16 level, on packed words (the generic item's steps, same results).
+template <int MA, int MB, int SG>
+__device__ void packed_first_item(const PassDesc &d, int gy, int tile, uint16_t *sm) {
+    constexpr int M = MA + MB, RA = 1 << MA, RB = 1 << MB, PAD = 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const TileGeom G = tile_geom(MA, MB, d.n_a, nwarps, PAD);
+    const int T = G.tile_out, P = G.pitch;
+    const ItemPos ip = item_pos<M, SG, false, 0>(d, T, gy, tile);
+    // block A: image rows -> MA levels -> shared tile (packed words)
+    for (int item = warp; item < RB * G.n_a; item += nwarps) {
+        const int g = item % RB, wc = item / RB;
+        const int i0 = wc * kWarpValid + lane * kV;
+        uint32_t w[RA][4];
+        load_block_a_u8x2<SG, RA>(d, M, ip.S, g * RA, ip.A_off, wc * kWarpValid, i0, w);
+        reg_butterfly_u16x2<MA>(w);
+        if (lane < kLanesValid) {
+            const int pos = (8 + PAD) * (i0 >> 3);
+#pragma unroll
+            for (int c = 0; c < RA; ++c) {
+                uint32_t *row = reinterpret_cast<uint32_t *>(sm + (g * RA + c) * P + pos);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) row[j] = w[c][j];
+            }
+        }
+    }
+    __syncthreads();
+    // block B: level-MA slope a2 of every mini-strip -> MB levels -> the level
+    for (int item = warp; item < RA * G.n_b; item += nwarps) {
+        const int a2 = item % RA, jc = item / RA;
+        const int slope0 = (ip.a << M) + a2 * RB;
+        if (slope0 > d.need_hi || slope0 + RB - 1 < d.need_lo) continue;
+        const int i0 = jc * kWarpValid + lane * kV;
+        const int i0r = i0 < T ? i0 : T;
+        uint32_t w[RB][4];
+#pragma unroll
+        for (int g = 0; g < RB; ++g) {
+            const int x0 = i0r + a2 * g;
+            tile_read_u16x2(sm + (g * RA + a2) * P + tile_pos(x0 & ~7, PAD), x0 & 7, w[g]);
+        }
+        reg_butterfly_u16x2<MB>(w);
+        if (lane < kLanesValid && i0 < T) {
+            const DestCols dc = dest_cols<SG, 0, int32_t, uint16_t>(d, ip.D, i0);
+            uint16_t *row = reinterpret_cast<uint16_t *>(d.hi.ptr) +
+                            (int64_t)hi_row(d, M, ip.S, ip.a, a2 * RB) * d.hi.pitch;
+            if (dc.vec) {
+                uint16_t *p = row + dc.lo;
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    uint4 q;
+                    if constexpr (SG > 0) {
+                        q = make_uint4(w[r][0], w[r][1], w[r][2], w[r][3]);
+                    } else {   // ascending columns: words and halves reversed
+                        q = make_uint4(__byte_perm(w[r][3], 0u, 0x1032u),
+                                       __byte_perm(w[r][2], 0u, 0x1032u),
+                                       __byte_perm(w[r][1], 0u, 0x1032u),
+                                       __byte_perm(w[r][0], 0u, 0x1032u));
+                    }
+                    uint16_t *pr = p + (int64_t)r * d.hi.pitch;
+                    if (FHT_STORE_OK(pr, 16)) *reinterpret_cast<uint4 *>(pr) = q;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    int32_t asc[kV];
+#pragma unroll
+                    for (int k = 0; k < kV; ++k) {
+                        const int kb = SG > 0 ? k : kV - 1 - k;   // buffer column
+                        asc[k] = (int32_t)((w[r][kb >> 1] >> (16 * (kb & 1))) & 0xffffu);
+                    }
+                    store8<uint16_t, int32_t>(row + (int64_t)r * d.hi.pitch, dc.lo, d.hi.cols, asc);
+                }
+            }
+        }
+    }
+}
+
 // One item with all the CTA's warps: single register block (MB = 0), or
 // block A, a CTA barrier, block B.
 // ADJ selects the adjoint form at compile time (cyclic columns, row-mapped
@@ -1461,6 +1621,13 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
     constexpr int M = MA + MB, RA = 1 << MA;
     constexpr int PAD = TilePad<MidE>::kPad;
     FHT_DEBUG_BEGIN(d);
+    // the first pass of a sum over a uint8 image into a uint16 level: packed
+    if constexpr (!ADJ && FIN == 0 && OP == 0 && MB > 0 && NC &&
+                  std::is_same<Acc, int32_t>::value && std::is_same<SrcE, uint8_t>::value &&
+                  std::is_same<MidE, uint16_t>::value && std::is_same<DstE, uint16_t>::value) {
+        packed_first_item<MA, MB, SG>(d, gy, tile, sm);
+        return;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const TileGeom G = tile_geom(MA, MB, d.n_a, nwarps, PAD);
