@@ -1622,7 +1622,8 @@ __device__ void fused_forward_item(const PassDesc &d, int gy, int tile, MidE *sm
     constexpr int PAD = TilePad<MidE>::kPad;
     FHT_DEBUG_BEGIN(d);
     // the first pass of a sum over a uint8 image into a uint16 level: packed
-    if constexpr (!ADJ && FIN == 0 && OP == 0 && MB > 0 && NC &&
+    // (its source is the caller's image, read-only in any launch)
+    if constexpr (!ADJ && FIN == 0 && OP == 0 && MB > 0 &&
                   std::is_same<Acc, int32_t>::value && std::is_same<SrcE, uint8_t>::value &&
                   std::is_same<MidE, uint16_t>::value && std::is_same<DstE, uint16_t>::value) {
         packed_first_item<MA, MB, SG>(d, gy, tile, sm);
