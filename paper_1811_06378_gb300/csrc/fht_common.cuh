@@ -128,9 +128,11 @@ __host__ __device__ inline int wrap_w(int v, int W) {
 // columns before that column, on a multiple of 8: a lane's 8 columns that
 // hold any needed column then start inside the window (no wrap), and
 // aligned rows stay aligned.
+__host__ __device__ inline int win_base_raw(const PassDesc &d, int s, int a) {
+    return wrap_w(d.win_c + d.sigma * a * s - 8, d.W);
+}
 __host__ __device__ inline int win_base(const PassDesc &d, int s, int a) {
-    const int b = wrap_w(d.win_c + d.sigma * a * s - 8, d.W);
-    return b & ~7;
+    return win_base_raw(d, s, a) & ~7;
 }
 
 // fhtshift rotation of slope row t (Section 5): the w_in + t meaningful

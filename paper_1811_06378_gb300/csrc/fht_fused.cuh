@@ -892,10 +892,28 @@ __device__ __forceinline__ void store_rows_win(const PassDesc &d, int k1, int lo
     DstE *base = reinterpret_cast<DstE *>(d.hi.ptr);
     const int mask = (1 << k1) - 1;
     const bool whole = lo + kV <= W;
+    // The R rows are consecutive slopes of one strip s: their windows start
+    // sigma*s apart. x is row r's unrounded start, win_c + sigma*(a + r)*s - 8
+    // (mod W), advanced by one add and one wrap per row (s < W).
+    const int s = hi_r0 >> k1;
+    int x = win_base_raw(d, s, hi_r0 & mask);
+    // lo and every window start are multiples of 8: with W one too, a row's
+    // 8 columns inside its window are one aligned vector
+    const bool vec_ok = (W & 7) == 0 && ((d.hi.pitch * (int64_t)sizeof(DstE)) & 15) == 0 &&
+                        (reinterpret_cast<uintptr_t>(base) & 15) == 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+        if (r > 0) {
+            if constexpr (SG > 0) {
+                x += s;
+                if (x >= W) x -= W;
+            } else {
+                x -= s;
+                if (x < 0) x += W;
+            }
+        }
         const int row = hi_r0 + r;
-        const int b = win_base(d, row >> k1, row & mask);
+        const int b = x & ~7;
         int j = lo - b;
         if (j < 0) j += W;
         if (whole && j >= L && j + kV <= W) continue;   // all 8 outside the window
@@ -904,7 +922,8 @@ __device__ __forceinline__ void store_rows_win(const PassDesc &d, int k1, int lo
         for (int k = 0; k < kV; ++k) asc[k] = SG > 0 ? v[r][k] : v[r][kV - 1 - k];
         DstE *rp = base + (int64_t)row * d.hi.pitch;
         if (whole && j + kV <= L) {
-            store8<DstE, Acc>(rp, j, L, asc);
+            if (vec_ok) store8_vec<DstE, Acc>(rp + j, asc);
+            else store8<DstE, Acc>(rp, j, L, asc);
         } else {
             Vec8<Acc> e;
 #pragma unroll
