@@ -318,7 +318,10 @@ fht_status fht_shear_range(double phi_lo, double phi_hi, int h, int w, fht_quadr
  * then shear), on the cyclic width W = w_alpha + n:
  *   Hs[t][x] = sum_{y<n} S[y][(x + sigma*off_n(t,y) - s(y)) mod W],
  * S the scaled image zero-padded to W columns. A line with dx/dy = k lies on
- * slope alpha*k + spl. Every intermediate level is all W columns wide. */
+ * slope alpha*k + spl. Every intermediate level is all W columns wide. The
+ * library writes S once into the workspace (one gather kernel) and runs the
+ * sheared transform on it: the same sums as scaling inside the first
+ * iteration, with the first pass reading whole vectors. */
 
 /* Scaled width w_alpha of a row of w pixels (HOST). FHT_EINVAL unless
  * 1/256 <= alpha <= 256 and 1 <= w_alpha <= 32768. */
@@ -329,7 +332,9 @@ fht_status fht_scaled_width(int w, double alpha, int *w_alpha);
 fht_status fht_scaled_shape(int h, int w, fht_quadrant q, double alpha, int *rows, int *cols);
 
 /* Workspace bytes of fht_forward_scaled for this size, quadrant, factor and
- * types. */
+ * types: the intermediate levels and, after them, the scaled copy of the
+ * image the first pass reads (h x w_alpha for Q0/Q1, w_alpha x w for Q2/Q3,
+ * rows padded to 16 bytes). */
 fht_status fht_workspace_size_scaled(int h, int w, fht_quadrant q, double alpha,
                                      fht_dtype in_t, fht_dtype acc_t, size_t *bytes);
 

@@ -1075,14 +1075,13 @@ fht_status fht_workspace_size_sheared(int h, int w, fht_quadrant q, fht_dtype in
     return FHT_OK;
 }
 
-// The sheared (and optionally scaled) forward transform of Section 4 on the
-// cyclic pass code: every pass carries the shear in fixed point (shear_p) and
-// the scale step (0 = none); P was built with sheared = true (and the scaled
-// width).
+// The sheared forward transform of Section 4 on the cyclic pass code: every
+// pass carries the shear in fixed point (shear_p); P was built with sheared =
+// true (for the scaled transform, on the scaled width, img being the scaled
+// copy).
 static fht_status run_sheared(const QuadPlan &P, const void *img, int in_elem, int64_t in_pitch,
-                              long long shear_p, long long scale_step, int t_lo, int t_hi,
-                              void *out, fht_dtype acc_t, int64_t out_pitch, void *workspace,
-                              cudaStream_t st) {
+                              long long shear_p, int t_lo, int t_hi, void *out, fht_dtype acc_t,
+                              int64_t out_pitch, void *workspace, cudaStream_t st) {
     const int acc = P.acc_elem;
     Side image{const_cast<void *>(img), in_pitch, in_elem, P.h_c, P.w_c};
     Side o{out, out_pitch, elem_of(acc_t), 0, P.W};
@@ -1090,7 +1089,6 @@ static fht_status run_sheared(const QuadPlan &P, const void *img, int in_elem, i
         PassDesc d = pass_desc(P, p, image, o, workspace, quadrant_map(t_lo, t_hi), t_lo, t_hi);
         d.shear_on = 1;
         d.shear_p = shear_p;
-        d.scale_step = scale_step;
         if (d.hi_final) {
             // every column X of the slope rows [t_lo, t_hi]: p = X + sigma_plus * n
             d.dst_image = 1;
@@ -1142,7 +1140,7 @@ fht_status fht_forward_sheared(const void *img, fht_dtype in_t, int h, int w, in
     if (t_lo < 0 || t_hi < t_lo || t_hi >= P.n || out_pitch < P.W) return FHT_EINVAL;
     const size_t need = plan_workspace(P);
     if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
-    return run_sheared(P, img, in_elem, in_pitch, shear_fixed(spl), 0, t_lo, t_hi, out, acc_t,
+    return run_sheared(P, img, in_elem, in_pitch, shear_fixed(spl), t_lo, t_hi, out, acc_t,
                        out_pitch, workspace, (cudaStream_t)stream);
 }
 
@@ -1179,6 +1177,31 @@ fht_status fht_scaled_shape(int h, int w, fht_quadrant q, double alpha, int *row
     return FHT_OK;
 }
 
+// The scaled copy of the image the scaled transform reads, placed in the
+// workspace after the plan's level buffers: Q0/Q1 scale every image row to
+// w_alpha columns (h x w_alpha), Q2/Q3 the image's row index (w_alpha x w
+// rows, read transposed); rows padded to 16 bytes.
+struct ScaledCopy {
+    bool along_rows;
+    int rows, cols;
+    int64_t pitch;   // elements
+    size_t offset, bytes;
+};
+
+static ScaledCopy scaled_copy(const QuadPlan &P, int h, int w, fht_quadrant q, int wa,
+                              int in_elem) {
+    ScaledCopy c;
+    const int eb = (int)elem_bytes(in_elem);
+    c.along_rows = q >= 2;
+    c.rows = c.along_rows ? wa : h;
+    c.cols = c.along_rows ? w : wa;
+    const int g = 16 / eb;
+    c.pitch = ((int64_t)c.cols + g - 1) / g * g;
+    c.offset = (plan_workspace(P) + 255) / 256 * 256;
+    c.bytes = (size_t)c.rows * (size_t)c.pitch * (size_t)eb;
+    return c;
+}
+
 fht_status fht_workspace_size_scaled(int h, int w, fht_quadrant q, double alpha, fht_dtype in_t,
                                      fht_dtype acc_t, size_t *bytes) {
     if (!sizes_ok(h, w) || !quadrant_ok(q) || !bytes) return FHT_EINVAL;
@@ -1187,7 +1210,9 @@ fht_status fht_workspace_size_scaled(int h, int w, fht_quadrant q, double alpha,
     long long D = 0;
     int wa = 0;
     if (!scaled_geometry(q >= 2 ? h : w, alpha, &D, &wa)) return FHT_EINVAL;
-    *bytes = plan_workspace(make_plan(h, w, q, false, elem_of(in_t), acc, false, true, 0, wa));
+    const QuadPlan P = make_plan(h, w, q, false, elem_of(in_t), acc, false, true, 0, wa);
+    const ScaledCopy c = scaled_copy(P, h, w, q, wa, elem_of(in_t));
+    *bytes = c.offset + c.bytes;
     return FHT_OK;
 }
 
@@ -1206,10 +1231,18 @@ fht_status fht_forward_scaled(const void *img, fht_dtype in_t, int h, int w, int
     QuadPlan P = make_plan(h, w, q, false, in_elem, acc, false, true, 0, wa);
     if (P.K > kMaxK) return FHT_EINVAL;
     if (t_lo < 0 || t_hi < t_lo || t_hi >= P.n || out_pitch < P.W) return FHT_EINVAL;
-    const size_t need = plan_workspace(P);
-    if (workspace_bytes < need || (need > 0 && !workspace)) return FHT_EINVAL;
-    return run_sheared(P, img, in_elem, in_pitch, shear_fixed(spl), D, t_lo, t_hi, out, acc_t,
-                       out_pitch, workspace, (cudaStream_t)stream);
+    const ScaledCopy c = scaled_copy(P, h, w, q, wa, in_elem);
+    if (!workspace || workspace_bytes < c.offset + c.bytes) return FHT_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    void *copy = static_cast<char *>(workspace) + c.offset;
+    const cudaError_t e = launch_scale_image(img, in_pitch, (int)elem_bytes(in_elem), c.along_rows,
+                                             D, copy, c.pitch, c.rows, c.cols, st);
+    if (e != cudaSuccess) {
+        g_last_cuda_error = (int)e;
+        return FHT_ECUDA;
+    }
+    return run_sheared(P, copy, in_elem, c.pitch, shear_fixed(spl), t_lo, t_hi, out, acc_t,
+                       out_pitch, workspace, st);
 }
 
 fht_status fht_scale_range(double phi_lo, double phi_hi, int h, int w, fht_quadrant *q,

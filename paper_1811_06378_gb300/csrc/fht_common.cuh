@@ -92,11 +92,6 @@ struct PassDesc {
     // quadrant's rows t in [dst_row_lo, dst_h), stored at row t - dst_row_lo.
     int shear_on, dst_row_lo;
     long long shear_p;
-    // Scaled forward (Section 4, the scale along the rows), set with
-    // shear_on: the level-0 row is the image row resampled by scale_step
-    // (D = ceil(2^32 / alpha)): column c < lo.cols (the scaled width) is image
-    // column (c * D) >> 32; 0 = no scale.
-    long long scale_step;
     // Host bookkeeping, not read by the kernels: the pass belongs to a range
     // transform (fht_forward_range, fht_forward_op with a slope range), whose
     // launches are named apart from those of whole quadrants.

@@ -553,53 +553,6 @@ __device__ __forceinline__ void load_block_a_sheared(const PassDesc &d, int row0
     }
 }
 
-// Scalar load; NC as in ldvec.
-template <bool NC, typename T>
-__device__ __forceinline__ T ldscalar(const T *p) {
-    if (!FHT_LOAD_OK(p, sizeof(T))) return T(0);
-    if constexpr (NC) return __ldg(p);
-    else return *p;
-}
-
-// Block A's source rows of a scaled (and sheared) forward's first pass: row
-// y of the level-0 array at column x is the scaled image row's column
-// c = (x - s(y)) mod W when c < lo.cols (the scaled width), which is image
-// column (c * scale_step) >> 32 (of image row y; for the transposed
-// quadrants, image column y of that image row), and zero otherwise. The
-// source columns are not contiguous (repeated or skipped), so each element
-// is its own load. Out of line: the adjoint kernels share this pass code, and
-// the gathers would otherwise grow their hot loop.
-template <int SG, int RA, typename Acc, typename SrcE, bool NC = true>
-__device__ __noinline__ Block<Acc, RA> load_block_a_scaled(const PassDesc &d, int row0, int X) {
-    Block<Acc, RA> b;
-    auto &v = b.x;
-    const SrcE *img = reinterpret_cast<const SrcE *>(d.lo.ptr);
-    const unsigned long long step = (unsigned long long)d.scale_step;
-#pragma unroll
-    for (int r = 0; r < RA; ++r) {
-        const int y = row0 + r;
-        if (y >= d.lo.rows) {
-#pragma unroll
-            for (int k = 0; k < kV; ++k) v[r][k] = Acc(0);
-            continue;
-        }
-        int c = wrap_w(X - shear_shift(d, y), d.W);
-#pragma unroll
-        for (int k = 0; k < kV; ++k) {
-            Acc val = Acc(0);
-            if (c < d.lo.cols) {
-                const int64_t sc = (int64_t)(((unsigned long long)c * step) >> 32);
-                val = d.transpose ? (Acc)ldscalar<NC>(img + sc * d.lo.pitch + y)
-                                  : (Acc)ldscalar<NC>(img + (int64_t)y * d.lo.pitch + sc);
-            }
-            v[r][k] = val;
-            if (++c == d.W) c = 0;
-        }
-        if constexpr (SG < 0) reverse8(v[r]);
-    }
-    return b;
-}
-
 // Block A's RA source rows s0.. for this lane's 8 buffer columns i0..i0+7.
 // Whether every row and every lane of the warp item (columns wbase ..
 // wbase + 255) lies inside the source is decided once, warp-uniformly; the
@@ -614,15 +567,6 @@ __device__ __forceinline__ void load_block_a(const PassDesc &d, int M, int S, in
             // sheared forward, first pass: a = 0 (level 0 has one slope)
             const int p_first = A_off + sg * i0;
             const int X = (sg > 0 ? p_first : p_first - (kV - 1)) - splus;
-            if (d.scale_step) {
-                const Block<Acc, RA> b =
-                    load_block_a_scaled<SG, RA, Acc, SrcE, NC>(d, S * (1 << M) + s0, X);
-#pragma unroll
-                for (int r = 0; r < RA; ++r)
-#pragma unroll
-                    for (int k = 0; k < kV; ++k) v[r][k] = b.x[r][k];
-                return;
-            }
             // ascending columns of the whole warp item: [Xw0, Xw1)
             const int Xw0 = sg > 0 ? A_off + wbase - splus : A_off - wbase - (32 * kV - 1);
             load_block_a_sheared<SG, RA, Acc, SrcE, NC>(d, S * (1 << M) + s0, X, Xw0,

@@ -64,6 +64,18 @@ constexpr int fused_min_blocks() {
     return 24 / kFusedWarps;
 }
 
+// The cyclic (adjoint-form) passes run at two CTAs per SM (128 registers):
+// at 80 the final ones, whose image-gradient stores hold the old values of
+// several rows, spill about 0.5 KB per thread, and the adjoint's first pass
+// from an FP32 gradient ran 8% slower at three (4096^2: 62.7 -> 67.7 us). The
+// first passes of the sheared and scaled transforms, from a uint8 image or a
+// uint16 level into a level, gain at three (the +-15 degree sheared quadrant
+// 84.0 -> 80.6 us).
+template <int FIN, typename SrcE>
+constexpr int adjoint_min_blocks() {
+    return (FIN == 0 && sizeof(SrcE) < 4 ? 24 : 16) / kFusedWarps;
+}
+
 template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE, int OP = 0>
 __global__ void __launch_bounds__(kFusedWarps * 32, fused_min_blocks<MidE>())
@@ -75,7 +87,7 @@ __global__ void __launch_bounds__(kFusedWarps * 32, fused_min_blocks<MidE>())
 
 template <int MA, int MB, int SG, int FIN, typename Acc, typename SrcE, typename MidE,
           typename DstE>
-__global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
+__global__ void __launch_bounds__(kFusedWarps * 32, adjoint_min_blocks<FIN, SrcE>())
     fused_adjoint_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_forward_item<MA, MB, SG, true, FIN, Acc, SrcE, MidE, DstE>(
@@ -84,10 +96,12 @@ __global__ void __launch_bounds__(kFusedWarps * 32, 16 / kFusedWarps)
 
 // Uniform batch: image blockIdx.z of `d.batch` same-size transforms. The
 // CTA's pass descriptor, with that image's source and destination, lives in
-// shared memory (thread 0 writes it) and the item reads it there.
+// shared memory (thread 0 writes it) and the item reads it there. (A local
+// copy of the parameter with the two pointers changed goes to the stack.)
 template <int MA, int MB, int SG, int FIN, bool ADJ, typename Acc, typename SrcE, typename MidE,
           typename DstE>
-__global__ void __launch_bounds__(kFusedWarps * 32, fused_min_blocks<MidE>())
+__global__ void __launch_bounds__(kFusedWarps * 32,
+                                  ADJ ? adjoint_min_blocks<FIN, SrcE>() : fused_min_blocks<MidE>())
     fused_batch_kernel(PassDesc d) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ PassDesc s_d;

@@ -49,10 +49,9 @@ inline size_t elem_size(int type) { return type == kU8 ? 1 : type == kU16 ? 2 : 
 
 // The spans a pass may touch (PassDesc::dbg_lo_bytes / dbg_hi_bytes), from
 // the descriptor's own geometry: a level buffer is n rows of its pitch; the
-// caller's image is its rows x columns view (transposed for Q2/Q3, the
-// unscaled width for the scaled transform); a gradient source covers the
-// rows its row map reaches; a destination covers the rows and columns its
-// map writes. Only the debug build reads them.
+// caller's image is its rows x columns view (transposed for Q2/Q3); a
+// gradient source covers the rows its row map reaches; a destination covers
+// the rows and columns its map writes. Only the debug build reads them.
 inline void set_debug_extents(PassDesc &d) {
     const long long le = (long long)elem_size(d.lo.type), he = (long long)elem_size(d.hi.type);
     long long lo = 0, hi = 0;
@@ -63,8 +62,7 @@ inline void set_debug_extents(PassDesc &d) {
         const long long r1 = d.src_row_base + (long long)d.src_row_dir * d.src_t_last;
         lo = ((r0 > r1 ? r0 : r1) * d.lo.pitch + d.W) * le;
     } else {
-        long long cols = d.lo.cols;
-        if (d.scale_step) cols = (((long long)d.lo.cols - 1) * d.scale_step >> 32) + 1;
+        const long long cols = d.lo.cols;
         const long long mr = d.transpose ? cols : d.lo.rows, mc = d.transpose ? d.lo.rows : cols;
         lo = ((mr - 1) * d.lo.pitch + mc) * le;
     }
@@ -134,5 +132,15 @@ cudaError_t launch_min_i32_u8_i32(int M, const PassDesc &d, cudaStream_t st);
 cudaError_t launch_min_i32_u16_u16(int M, const PassDesc &d, cudaStream_t st);
 cudaError_t launch_min_i32_u16_i32(int M, const PassDesc &d, cudaStream_t st);
 cudaError_t launch_min_f32(int M, const PassDesc &d, cudaStream_t st);
+
+// Nearest-neighbour scale of a rows x cols image (elements of elem bytes,
+// pitches in elements) by the 32.32 step D along one axis (Section 4):
+// dst[r][c] = src[r][(c * D) >> 32] (along_rows false: every row scaled to
+// out_cols columns) or src[(r * D) >> 32][c] (true: out_rows rows, each a
+// copy of its source row). Every source index stays below the source's
+// extent when out_cols (out_rows) is the scaled width of fht_scaled_width.
+cudaError_t launch_scale_image(const void *src, int64_t src_pitch, int elem, bool along_rows,
+                               long long D, void *dst, int64_t dst_pitch, int out_rows,
+                               int out_cols, cudaStream_t st);
 
 }  // namespace fht

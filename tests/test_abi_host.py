@@ -232,8 +232,20 @@ def test_scaled_bad_arguments_rejected_on_host(fht):
     assert L.fht_forward_scaled(*args(2.0, 0.0, 0, 7, 23)) == EINVAL
     n = ctypes.c_size_t()
     assert L.fht_workspace_size_scaled(4096, 2048, 0, 2.0, U8, I32, ctypes.byref(n)) == 0
-    # two passes: one full-width level of n x W (W = 4096 + 4096), uint16
-    assert n.value == 4096 * 8192 * 2
+    # two passes: one full-width level of n x W (W = 4096 + 4096), uint16, then
+    # the scaled copy of the image (h x w_alpha bytes)
+    assert n.value == 4096 * 8192 * 2 + 4096 * 4096
+    # alpha = 1: the sheared transform's levels, then the copy, its rows padded
+    # to 16 bytes (Q0: 300 rows of 2001 -> 2016 uint8; Q2 scales the image's
+    # row index: 300 rows of 2001 -> 2004 FP32 values)
+    m = ctypes.c_size_t()
+    F32 = 2
+    for q, copy in ((0, 300 * 2016), (2, 300 * 2004 * 4)):
+        dt = U8 if q == 0 else F32
+        acc = I32 if q == 0 else F32
+        assert L.fht_workspace_size_sheared(300, 2001, q, dt, acc, ctypes.byref(m)) == 0
+        assert L.fht_workspace_size_scaled(300, 2001, q, 1.0, dt, acc, ctypes.byref(n)) == 0
+        assert n.value == (m.value + 255) // 256 * 256 + copy, q
 
 
 @pytest.mark.parametrize("q", [0, 1, 2, 3])
