@@ -52,27 +52,28 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
     return v;
 }
 
-// Sources are read with coherent loads (NC = false): a second pass reads the
-// level its image's first pass wrote earlier in this same launch.
+// A pass that reads a level reads it with coherent loads (NC = false): its
+// image's earlier pass wrote it in this same launch. Passes from the caller's
+// image (NC = true) read it through the non-coherent path: nothing writes it.
 template <int MA, int MB, int SG, bool ADJ, int FIN, typename Acc, typename SrcE, typename MidE,
-          typename DstE>
+          typename DstE, bool NC>
 __device__ __forceinline__ void run_item(const PassDesc &d, int gy, int tile, unsigned char *sm) {
-    fused_forward_item<MA, MB, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, 0, false>(
+    fused_forward_item<MA, MB, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, 0, NC>(
         d, gy, tile, reinterpret_cast<MidE *>(sm));
 }
 
 template <int SG, int FIN, typename Acc, typename SrcE, typename MidE, typename DstE,
-          bool ADJ = false>
+          bool ADJ = false, bool NC = false>
 __device__ __forceinline__ void run_item_m(int m, const PassDesc &d, int gy, int tile,
                                            unsigned char *sm) {
     switch (m) {
-    case 0: run_item<0, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 1: run_item<1, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 2: run_item<2, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 3: run_item<3, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 4: run_item<3, 1, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    case 5: run_item<3, 2, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
-    default: run_item<3, 3, SG, ADJ, FIN, Acc, SrcE, MidE, DstE>(d, gy, tile, sm); break;
+    case 0: run_item<0, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, NC>(d, gy, tile, sm); break;
+    case 1: run_item<1, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, NC>(d, gy, tile, sm); break;
+    case 2: run_item<2, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, NC>(d, gy, tile, sm); break;
+    case 3: run_item<3, 0, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, NC>(d, gy, tile, sm); break;
+    case 4: run_item<3, 1, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, NC>(d, gy, tile, sm); break;
+    case 5: run_item<3, 2, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, NC>(d, gy, tile, sm); break;
+    default: run_item<3, 3, SG, ADJ, FIN, Acc, SrcE, MidE, DstE, NC>(d, gy, tile, sm); break;
     }
 }
 
@@ -81,9 +82,9 @@ __device__ __forceinline__ void run_item_m(int m, const PassDesc &d, int gy, int
 // Thread 0 claims the next item while the CTA works on the current one (the
 // claim's latency is hidden), finds its segment and waits for its dependency;
 // all threads then copy the segment's pass descriptor (complete, pointers
-// included, written by the host) into shared memory. After an item thread 0
-// alone fences and counts it done: the CTA barrier before it orders every
-// thread's stores before that release.
+// included, written by the host) into shared memory. After an item one thread
+// of the last warp alone fences and counts it done: the CTA barrier before it
+// orders every thread's stores before that release.
 // Holding one claimed item ahead keeps the waits finite: the smallest
 // unfinished item is always some CTA's current item, and everything it
 // depends on has a smaller index.
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(kWarps * 32, MINB)
         }
         __syncthreads();
         const bool skip = s_skip != 0;
+        const int done_at = s_done;   // thread 0 rewrites s_done for the next item
         if (!skip) {
             const PassDesc &d = s_desc;
             const int m = s_m, tiles = s_tiles;
@@ -179,12 +181,12 @@ __global__ void __launch_bounds__(kWarps * 32, MINB)
                     // level; a uint16 level's pass is the last (two passes at most)
                     switch (s_variant) {
                     case kVarU8Final:
-                        run_item_m<SG, 1, int32_t, uint8_t, uint16_t, int32_t>(m, d, gy, tile,
-                                                                              smem_raw);
+                        run_item_m<SG, 1, int32_t, uint8_t, uint16_t, int32_t, false, true>(
+                            m, d, gy, tile, smem_raw);
                         break;
                     case kVarU8Level:
-                        run_item_m<SG, 0, int32_t, uint8_t, uint16_t, uint16_t>(m, d, gy, tile,
-                                                                               smem_raw);
+                        run_item_m<SG, 0, int32_t, uint8_t, uint16_t, uint16_t, false, true>(
+                            m, d, gy, tile, smem_raw);
                         break;
                     default:
                         run_item_m<SG, 1, int32_t, uint16_t, int32_t, int32_t>(m, d, gy, tile,
@@ -195,9 +197,11 @@ __global__ void __launch_bounds__(kWarps * 32, MINB)
             }
         }
         __syncthreads();   // every thread's stores of this item precede the release below
-        if (threadIdx.x == 0 && !skip) {
+        // The release is made by the last warp, so that its fence overlaps
+        // thread 0's claim, search and wait for the next item.
+        if (threadIdx.x == (kWarps - 1) * 32 && !skip) {
             __threadfence();
-            atomicAdd(done + s_done, 1u);
+            atomicAdd(done + done_at, 1u);
         }
     }
 }
