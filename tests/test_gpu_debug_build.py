@@ -65,6 +65,11 @@ for (h, w), gg, o in zip(shapes, grads, fplan.adjoint(grads)):
 big = edges_and_lines(4096, 700, seed=7)
 xb = torch.from_numpy(big).cuda()
 assert (fht.forward(xb, 0).cpu().numpy() == O.quadrant(big, 0)).all()   # the staged final pass
+for q, (h, w) in ((0, (4096, 700)), (2, (700, 4096))):   # the staged adjoint final passes
+    gb = torch.from_numpy(np.random.default_rng(8 + q).standard_normal(fht.query_shape(h, w, q))
+                          .astype(np.float32)).cuda()
+    assert np.array_equal(fht.adjoint(gb, h, w, fht.LAYOUT_QUADRANT, q).cpu().numpy(),
+                          O.adjoint_quadrant(gb.cpu().numpy(), h, w, q, "f32"))
 p = sharded.ShardPlan(1500, 700, 1, 4)
 Ls = [sharded.local_levels_gpu(p.strip_of(torch.from_numpy(big[:1500]).cuda(), r), p,
                                torch.int32) for r in range(4)]
