@@ -102,3 +102,19 @@ def test_scaled_view_with_pitch(fht):
     img = base[5:150, 3:203]
     got = host(fht.forward_scaled(view, 1, 1.5, 0.1))
     assert (got == as_i32(O.scaled_quadrant(img, 1, 1.5, 0.1))).all()
+
+
+@pytest.mark.parametrize("h,w,q,alpha", [(1, 1, 0, 0.5), (1, 1, 2, 3.0), (1, 7, 1, 1 / 256),
+                                         (7, 1, 3, 1 / 256), (3, 300, 0, 100.0),
+                                         (300, 3, 2, 100.0), (5, 300, 1, 1 / 256),
+                                         (2, 2, 0, 256.0)])
+def test_scaled_extreme_factors_and_degenerate_shapes(fht, h, w, q, alpha):
+    """The ends of the factor range (1/256 leaves one or two scaled columns,
+    100 and 256 widen a row to 30000 and 512 columns) on one-pixel, one-row
+    and one-column images, through all four quadrants; the scaled copy and
+    the transform against the oracle, bit for bit."""
+    img = edges_and_lines(h, w, seed=h * 31 + w)
+    got = host(fht.forward_scaled(dev(img), q, alpha, 0.3))
+    want = O.scaled_quadrant(img, q, alpha, 0.3)
+    assert got.shape == want.shape
+    assert (got == as_i32(want)).all(), (h, w, q, alpha)
