@@ -77,9 +77,71 @@ __global__ void __launch_bounds__(kScaleThreads)
     }
 }
 
+// uint8 rows, alpha >= 1/2 (D <= 2^33): a block's kSpanOut output columns
+// take at most 2 * kSpanOut + 1 consecutive source bytes. The block loads
+// that span once into shared memory as aligned 4-byte words (coalesced; the
+// source and its pitch are 4-byte aligned, so the words stay inside the
+// row's pitch), then every thread gathers 16 output bytes from shared memory
+// and stores them as one 16-byte vector.
+constexpr int kSpanPer = 16;                              // output bytes per thread
+constexpr int kSpanOut = kScaleThreads * kSpanPer;        // output bytes per block
+constexpr int kSpanWords = (2 * kSpanOut + 1 + 6) / 4 + 1;  // aligned words of the span
+
+__global__ void __launch_bounds__(kScaleThreads)
+    scale_cols_u8_span_kernel(const uint8_t *__restrict__ src, int64_t sp, unsigned long long D,
+                              uint8_t *__restrict__ dst, int64_t dp, int out_cols) {
+    __shared__ uint32_t span[kSpanWords];
+    const int r = blockIdx.y;
+    const int b0 = blockIdx.x * kSpanOut;
+    const int b1 = (b0 + kSpanOut < out_cols ? b0 + kSpanOut : out_cols) - 1;   // last column
+    const long long s_lo = (long long)(((unsigned long long)b0 * D) >> 32);
+    const long long s_hi = (long long)(((unsigned long long)b1 * D) >> 32);
+    const long long a0 = s_lo & ~3LL;                  // first aligned word (bytes)
+    const int nw = (int)(((s_hi + 4) & ~3LL) - a0) / 4;   // words up to the one holding s_hi
+    const uint32_t *srow = reinterpret_cast<const uint32_t *>(src + (int64_t)r * sp + a0);
+    for (int i = threadIdx.x; i < nw; i += kScaleThreads) span[i] = __ldg(srow + i);
+    __syncthreads();
+    const uint8_t *sb = reinterpret_cast<const uint8_t *>(span);
+    const int c0 = b0 + threadIdx.x * kSpanPer;
+    if (c0 >= out_cols) return;
+    unsigned long long acc = (unsigned long long)c0 * D;
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + 4 * j + k;
+            const long long sc = (long long)(acc >> 32);
+            acc += D;
+            const uint32_t b = c < out_cols ? (uint32_t)sb[sc - a0] : 0u;
+            word |= b << (8 * k);
+        }
+        w[j] = word;
+    }
+    uint8_t *drow = dst + (int64_t)r * dp;
+    if (c0 + kSpanPer <= out_cols && (reinterpret_cast<uintptr_t>(drow + c0) & 15) == 0) {
+        *reinterpret_cast<uint4 *>(drow + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kSpanPer; ++k)
+            if (c0 + k < out_cols) drow[c0 + k] = (uint8_t)(w[k >> 2] >> (8 * (k & 3)));
+    }
+}
+
 template <typename T>
 cudaError_t launch_t(const void *src, int64_t sp, bool along_rows, long long D, void *dst,
                      int64_t dp, int out_rows, int out_cols, cudaStream_t st) {
+    if constexpr (sizeof(T) == 1) {
+        if (!along_rows && (unsigned long long)D <= (1ULL << 33) && sp % 4 == 0 &&
+            (reinterpret_cast<uintptr_t>(src) & 3) == 0) {
+            const dim3 grid((unsigned)((out_cols + kSpanOut - 1) / kSpanOut), (unsigned)out_rows);
+            scale_cols_u8_span_kernel<<<grid, kScaleThreads, 0, st>>>(
+                static_cast<const uint8_t *>(src), sp, (unsigned long long)D,
+                static_cast<uint8_t *>(dst), dp, out_cols);
+            return cudaGetLastError();
+        }
+    }
     const int per_block = kScaleThreads * kScalePer;
     const dim3 grid((unsigned)((out_cols + per_block - 1) / per_block), (unsigned)out_rows);
     const T *s = static_cast<const T *>(src);
